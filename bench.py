@@ -1,0 +1,359 @@
+"""Benchmark of the fused DG shallow-water stage on one GB300 (or N replicas).
+
+Metric: DOF-updates/s per RK stage (DOF = 3 (p+1)^2 nlon nlat, one update per
+DOF per Runge-Kutta stage).  One bench step is the workload of the 180 x 90,
+degree 3 configuration: 1000 SSP-RK3 time steps (3000 fused stage kernels,
+replayed from one captured CUDA graph) plus the compensated mass reduction,
+on the seeded synthetic field (depth 5960 m + 200 m of random spherical
+harmonics l <= 4, flow from a random stream function, |u| <= 20 m/s).  L2 is
+flushed (256 MiB write) before every timed step; each step is timed with CUDA
+events on the solver's stream.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun each rank runs an independent replica (weak scaling).
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    # name: (nlon, nlat, degree, rk steps per bench step, seed, description)
+    "c2": (180, 90, 3, 1000, 2, "180x90 elements, degree 3, SSP-RK3, 1000 steps per bench step, seed 2"),
+    "c1": (20, 10, 1, 100, 1, "20x10 elements, degree 1, SSP-RK3, 100 steps per bench step, seed 1"),
+    "c3": (360, 180, 4, 500, 3, "360x180 elements, degree 4, SSP-RK3, 500 steps per bench step, seed 3"),
+    "r1": (1440, 720, 4, 20, 3, "1440x720 elements, degree 4, SSP-RK3, 20 steps per bench step, seed 3"),
+}
+METRIC = "DOF-updates/s per RK stage (FP32/TC/learned vs FP64 plain) at stated L2 error"
+CFL = 0.1
+FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS))
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--rk-steps", type=int, default=0, help="override RK steps per bench step")
+    ap.add_argument("--no-extras", action="store_true", help="skip fp64-plain, e2e and cpu legs (profiling)")
+    return ap.parse_args()
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("gloo")
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def allreduce_max(world, x):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([x], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock and throttle-reason samples during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.device), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+            time.sleep(0.3)
+        except FileNotFoundError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            time.sleep(0.2)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = max(mx, float(parts[1]))
+            except ValueError:
+                continue
+            for name, flag in zip(names, parts[3:7]):
+                if flag.lower() in ("active", "1"):
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def initial_state(s, seed):
+    from paper_2303_11767_gb300 import synth
+
+    return s.project_grid(synth.SmoothField(seed, s.radius).fields_grid)
+
+
+def time_device(s, torch, stream, nsteps, dt, K, W, mass_t, flush):
+    """Per-step CUDA-event times (ms) of K timed bench steps after W warm-ups."""
+    times = []
+    with torch.cuda.stream(stream):
+        for it in range(W + K):
+            flush.zero_()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            s.step(nsteps, dt)
+            s.total_mass_device(mass_t)
+            b.record(stream)
+            if it >= W:
+                times.append((a, b))
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in times]
+
+
+def cpu_leg(nlon, nlat, p, seed, budget_s, max_steps):
+    """The FP64 oracle on the host cores: number of RK steps that fit the budget,
+    their wall time, and the resulting state."""
+    import oracle as O
+    from paper_2303_11767_gb300 import dgswe, synth
+
+    o = O.Oracle.sphere(nlon, nlat, p, synth.EARTH_RADIUS, dgswe.GRAVITY, dgswe.OMEGA)
+    cores = os.cpu_count() or 1
+    o.set_threads(cores)
+    u0 = o.project_tensor(synth.SmoothField(seed).fields_grid)
+    dt = o.max_dt(u0, CFL)
+    t0 = time.perf_counter()
+    o.rhs(u0)
+    t_rhs = time.perf_counter() - t0
+    nsteps = int(max(1, min(max_steps, budget_s / (3 * t_rhs))))
+    t0 = time.perf_counter()
+    u1 = o.step(u0, nsteps, dt, 3)
+    wall = time.perf_counter() - t0
+    return dict(o=o, u0=u0, u1=u1, dt=dt, nsteps=nsteps, wall=wall, cores=cores)
+
+
+def field_errors(x, y):
+    return [float(np.linalg.norm(x[..., f, :] - y[..., f, :]) / np.linalg.norm(y[..., f, :])) for f in range(3)]
+
+
+def run_reference(args, world, rank):
+    """Reference arm: the FP64 oracle timed on the host cores, each step a
+    bounded sample (a few RK steps) of the same workload."""
+    if rank != 0:
+        return
+    nlon, nlat, p, _, seed, desc = WORKLOADS[args.workload]
+    dof = 3 * (p + 1) ** 2 * nlon * nlat
+    import oracle as O
+    from paper_2303_11767_gb300 import dgswe, synth
+
+    o = O.Oracle.sphere(nlon, nlat, p, synth.EARTH_RADIUS, dgswe.GRAVITY, dgswe.OMEGA)
+    cores = os.cpu_count() or 1
+    o.set_threads(cores)
+    u = o.project_tensor(synth.SmoothField(seed).fields_grid)
+    dt = o.max_dt(u, CFL)
+    t0 = time.perf_counter()
+    o.rhs(u)
+    t_rhs = time.perf_counter() - t0
+    per = int(max(1, min(100, 3.0 / (3 * t_rhs))))     # ~3 s of work per step
+    times = []
+    for it in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        u = o.step(u, per, dt, 3)
+        if it >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    total = sum(times)
+    value = dof * 3 * per * len(times) / total
+    sample = f"{per} SSP-RK3 steps of the {desc.split(',')[0]} workload per step"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "DOF-updates/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / len(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": desc, "nlon": nlon, "nlat": nlat, "degree": p, "rk_steps_per_step": per},
+        "cpu_baseline": {"value": value, "unit": "DOF-updates/s", "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "DOF-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+    import torch
+
+    from paper_2303_11767_gb300 import dgswe
+
+    nlon, nlat, p, nsteps, seed, desc = WORKLOADS[args.workload]
+    if args.rk_steps:
+        nsteps = args.rk_steps
+    dof = 3 * (p + 1) ** 2 * nlon * nlat
+    torch.cuda.set_device(local)
+    dgswe.set_device(local)
+    stream = torch.cuda.Stream()   # shared by the solver, the L2 flush and the events
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    mass_t = torch.zeros(1, dtype=torch.float64, device="cuda")
+
+    def make(prec):
+        s = dgswe.Solver(nlon, nlat, p, precision=prec, check_finite=False)
+        s.set_option(dgswe.OPT_STREAM, stream.cuda_stream)
+        s.set_option(dgswe.OPT_STEPS_PER_GRAPH, min(nsteps, 1024))
+        return s
+
+    s = make(args.precision)
+    u0 = initial_state(s, seed)
+    s.set_state(u0)
+    dt = s.max_dt(CFL)
+    m0 = s.total_mass()
+
+    # ---- device-timed leg
+    torch.cuda.synchronize()
+    barrier(world)
+    launches0 = s.stage_launches()
+    with ClockSampler(local) as clk:
+        times = time_device(s, torch, stream, nsteps, dt, args.steps, args.warmup, mass_t, flush)
+    launches = s.stage_launches() - launches0
+    barrier(world)
+    total_ms = allreduce_max(world, sum(times))
+    stage_launches_timed = launches * args.steps // (args.steps + args.warmup)
+    m1 = s.total_mass()
+    s.set_option(dgswe.OPT_CHECK_FINITE, 1)
+    s.step(1, dt)                                          # raises if any stage met NaN / h <= 0
+    value = world * dof * 3 * nsteps * args.steps / (total_ms * 1e-3)
+    ms_per_step = total_ms / args.steps
+
+    # dominant kernel: the fused stage; algorithmic bytes per launch = the mean
+    # 8/3 state words per DOF of SSP-RK3 (u read by all stages, u^n by two, one write)
+    word = 4 if args.precision == "fp32" else 8
+    bytes_per_launch = dof * word * 8.0 / 3.0
+    launch_s = (sum(times) * 1e-3) / max(1, stage_launches_timed)
+    peak, peak_kind = peaks()
+    achieved = bytes_per_launch / launch_s / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": None, "peak_kind": peak_kind, "kernel": f"stage_kernel<{args.precision}, N={p + 1}>",
+                "bytes_per_launch": bytes_per_launch, "launch_us": launch_s * 1e6}
+
+    out = {
+        "metric": METRIC, "value": value, "unit": "DOF-updates/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64", "data": "synthetic",
+        "config": {"workload": desc, "nlon": nlon, "nlat": nlat, "degree": p, "dof": dof,
+                   "rk_steps_per_step": nsteps, "dt": dt, "cfl": CFL, "l2": "flushed before every timed step",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "roofline": roofline,
+        "gpu_launches": stage_launches_timed + 2 * args.steps,
+        "clocks": clk.summary(),
+        "mass_drift": (m1 - m0) / m0,
+    }
+
+    if not args.no_extras and rank == 0 and world == 1:
+        # ---- FP64 plain path on the same workload
+        s64 = make("fp64")
+        s64.set_state(u0)
+        k64 = max(2, args.steps // 5)
+        t64 = time_device(s64, torch, stream, nsteps, dt, k64, 1, mass_t, flush)
+        v64 = dof * 3 * nsteps * k64 / (sum(t64) * 1e-3)
+        out["fp64_plain"] = {"value": v64, "ms_per_step": sum(t64) / k64, "dtype": "f64", "steps": k64,
+                             "speedup_of_value": value / v64}
+
+        # ---- end to end through the C-ABI with pinned host buffers
+        hin = torch.empty(s.state_len, dtype=torch.float64, pin_memory=True).numpy()
+        hout = torch.empty(s.state_len, dtype=torch.float64, pin_memory=True).numpy()
+        hin[:] = u0.reshape(-1)
+        se = make(args.precision)
+        se.set_option(dgswe.OPT_CHECK_FINITE, 1)
+        for it in range(args.warmup + args.steps):
+            if it == args.warmup:
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+            se.set_state(hin)
+            se.step(nsteps, dt)
+            mass = se.total_mass()
+            hout[:] = se.get_state().reshape(-1)
+        e2e_s = time.perf_counter() - t0
+        out["e2e"] = {"value": dof * 3 * nsteps * args.steps / e2e_s, "unit": "DOF-updates/s",
+                      "h2d_bytes_per_step": int(hin.nbytes), "d2h_bytes_per_step": int(hout.nbytes) + 8,
+                      "ms_per_step": 1e3 * e2e_s / args.steps, "mass": mass}
+
+        # ---- the oracle on the host cores (bounded sample) and the L2 error
+        leg = cpu_leg(nlon, nlat, p, seed, budget_s=15.0, max_steps=nsteps)
+        cpu_value = dof * 3 * leg["nsteps"] / leg["wall"]
+        out["cpu_baseline"] = {"value": cpu_value, "unit": "DOF-updates/s", "cores": leg["cores"], "kind": "oracle",
+                               "sample": f"{leg['nsteps']} SSP-RK3 steps of the same workload "
+                                         f"({3 * leg['nsteps']} stages), FP64, {leg['cores']} threads",
+                               "seconds": leg["wall"]}
+        errs = {}
+        for prec in ("fp32", "fp64"):
+            sv = make(prec)
+            sv.set_state(leg["u0"])
+            sv.step(leg["nsteps"], leg["dt"])
+            errs[prec] = field_errors(sv.get_state(), leg["u1"])
+        out["l2_error_vs_oracle"] = {"steps": leg["nsteps"], "fields": ["h", "hu", "hv"], **errs}
+    if rank == 0:
+        print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

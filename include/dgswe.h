@@ -1,0 +1,178 @@
+/*
+ * dgswe.h -- C-ABI of libdgswe, a GB300 (sm_103a) solver for the rotating
+ * shallow water equations on the sphere, discretised by the modal
+ * Discontinuous Galerkin method of arxiv 2303.11767 (Sec. 2) and advanced by
+ * explicit SSP Runge-Kutta.
+ *
+ * Problem (paper Sec. 2, Eq. sph3 and the definitions of U, F, G, S after it):
+ *   d_t U + d_lambda F(U) + d_theta G(U) = S(U),   U = cos(theta) (h, hu, hv),
+ * on the longitude-latitude rectangle lambda in [0, 2 pi], theta in
+ * [-pi/2, pi/2], periodic in lambda, zero flux through the pole edges
+ * (Sec. 2 and Sec. 4.3).  Element (i, j) covers
+ *   lambda in [i dlam, (i+1) dlam],  theta in [-pi/2 + j dth, -pi/2 + (j+1) dth],
+ * dlam = 2 pi / nlon, dth = pi / nlat.  The unknowns are the modal
+ * coefficients of (h, hu, hv) in the tensor basis phi_m = L_a(xi) L_b(eta) of
+ * orthonormal Legendre polynomials L_k = sqrt((2k+1)/2) P_k, m = b (p+1) + a
+ * (Eq. basis_expansion); cos(theta) lives in the element mass matrix (Eq. ode
+ * and the cos(theta)-weighted M that follows it).
+ *
+ * State layout, everywhere in this API: double array of
+ *   len = nlat * nlon * 3 * (p+1)^2  values, index
+ *   ((j * nlon + i) * 3 + f) * (p+1)^2 + m,   f = 0 h, 1 hu, 2 hv.
+ *
+ * Conventions:
+ *   - Every call returns a dg_status and never aborts the process.
+ *   - Host pointers are borrowed for the duration of the call only; the
+ *     library copies what it keeps.
+ *   - The state stays resident on the GPU between calls (paper Sec. 5.2.3:
+ *     host-device traffic only at the start).
+ *   - Calls on one handle must not run concurrently from several threads.
+ *     Separate handles are independent.
+ *   - dg_last_error() describes the last failing call of the calling thread.
+ *   - An error returned by a CUDA call (DG_ECUDA) may leave the device
+ *     context unusable; destroy the handle.
+ */
+#ifndef DGSWE_H
+#define DGSWE_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dg_ctx *dg_handle;
+
+typedef enum {
+    DG_OK = 0,
+    DG_EINVAL = 1,          /* invalid argument (message in dg_last_error) */
+    DG_ENOMEM = 2,          /* host or device allocation failed */
+    DG_ECUDA = 3,           /* a CUDA runtime call failed */
+    DG_ENONFINITE = 4,      /* a NaN or Inf appeared in the state or tendency */
+    DG_ENONPHYSICAL = 5,    /* h <= 0 at a quadrature point (u = hu/h undefined) */
+    DG_ETIMEOUT = 6,        /* a bounded device-side wait gave up */
+    DG_EUNSUPPORTED = 7     /* valid request that this build does not implement */
+} dg_status;
+
+typedef enum {
+    DG_PREC_FP64 = 0,           /* all stage arithmetic in FP64 */
+    DG_PREC_FP32 = 1,           /* stage arithmetic in FP32, FP64 tables and mass sums */
+    DG_PREC_FP32_TC_BF16 = 2,   /* reserved: BF16 tensor-core contractions */
+    DG_PREC_FP32_TC_FP16 = 3    /* reserved: FP16 tensor-core contractions */
+} dg_precision;
+
+typedef enum {
+    DG_OPT_PRECISION = 1,        /* dg_precision; default DG_PREC_FP64.  Changing it
+                                    converts the resident state. */
+    DG_OPT_RK_ORDER = 2,         /* 1..4, the SSP RK schemes of Table "Butcher";
+                                    default 3 */
+    DG_OPT_CHECK_FINITE = 3,     /* 0/1, default 1: dg_step and dg_rhs report
+                                    DG_ENONFINITE / DG_ENONPHYSICAL */
+    DG_OPT_ALPHA_MODE = 4,       /* 0 local Rusanov alpha (default); 1 global
+                                    (returns DG_EUNSUPPORTED) */
+    DG_OPT_STREAM = 5,           /* cudaStream_t cast to long long; 0 = the
+                                    library's own non-blocking stream */
+    DG_OPT_STEPS_PER_GRAPH = 6   /* time steps captured per CUDA graph, 1..1024,
+                                    default 16 */
+} dg_option;
+
+/* Make CUDA device `device` current for the calling thread in this library
+ * (the device dg_create allocates on).  DG_EINVAL if it does not exist. */
+dg_status dg_set_device(int device);
+
+/* Create a solver for an nlon x nlat element mesh of degree p (0 <= p <= 4;
+ * p = 0 is the first-order finite-volume special case).  nlon >= 1, nlat >= 2,
+ * radius > 0, g > 0.  Builds the FP64 tables (Gauss-Legendre rules, Legendre
+ * tables, per-row cos(theta)-weighted mass matrices C_j and their inverses,
+ * Sec. 3.2 "DG solver: precomputation") and allocates the device buffers on
+ * the current CUDA device.  *out receives the handle (NULL on failure). */
+dg_status dg_create(int nlon, int nlat, int degree, double radius, double g, double omega,
+                    dg_handle *out);
+
+/* Free the handle and its device buffers.  NULL is accepted. */
+dg_status dg_destroy(dg_handle h);
+
+/* Set an option (see dg_option). */
+dg_status dg_set_option(dg_handle h, int key, long long value);
+
+/* Number of doubles in a state array: nlat * nlon * 3 * (degree+1)^2
+ * (0 for a NULL handle). */
+size_t dg_state_len(dg_handle h);
+
+/* Copy a modal state from host memory into the solver (layout above).
+ * len must equal dg_state_len(h).  Resets nothing else; the simulated time is
+ * kept (see dg_set_time). */
+dg_status dg_set_state(dg_handle h, const double *modal, size_t len);
+
+/* Copy the current modal state into caller-owned host memory; synchronises
+ * the solver's stream. */
+dg_status dg_get_state(dg_handle h, double *modal, size_t len);
+
+/* Same as dg_set_state / dg_get_state with a device pointer (FP64, same
+ * layout), ordered on the solver's stream. */
+dg_status dg_set_state_device(dg_handle h, const double *d_modal, size_t len);
+dg_status dg_get_state_device(dg_handle h, double *d_modal, size_t len);
+
+/* Tendency d(modal)/dt = M^{-1} h(modal) of Eq. (ode) for the given host
+ * state: the volume, source and edge integrals of the weak form (Eq. dg_parts)
+ * with the Rusanov flux (Eq. rusanov), then the inverse element mass matrix.
+ * Does not touch the resident state.  modal_in and tend_out are host arrays of
+ * length len = dg_state_len(h), layout above. */
+dg_status dg_rhs(dg_handle h, const double *modal_in, double *tend_out, size_t len);
+
+/* Advance the resident state by n >= 0 steps of size dt > 0 with the SSP
+ * Runge-Kutta scheme of order DG_OPT_RK_ORDER (Table "Butcher"), replaying a
+ * captured CUDA graph of fused stage kernels.  Adds n*dt to the simulated
+ * time.  With DG_OPT_CHECK_FINITE, synchronises and reports DG_ENONFINITE or
+ * DG_ENONPHYSICAL if any stage met a non-finite value or h <= 0. */
+dg_status dg_step(dg_handle h, int n, double dt);
+
+/* Total mass R^2 sum_k int h cos(theta) dlambda dtheta of the resident state
+ * (paper Sec. 2: the single-valued numerical flux conserves it), reduced on
+ * the GPU in FP64 with compensated (Neumaier) sums in a fixed order, so the
+ * result is reproducible bit for bit. */
+dg_status dg_total_mass(dg_handle h, double *mass);
+
+/* Same reduction, enqueued on the solver's stream without waiting: writes the
+ * total mass (one double) to the device pointer d_mass when the stream
+ * reaches it.  Usable inside CUDA graph capture of the solver's stream. */
+dg_status dg_total_mass_device(dg_handle h, double *d_mass);
+
+/* Largest stable step from the Courant number p c dt / H of Sec. 2:
+ *   H = min over elements and Gauss points of min(R dth, R cos(theta) dlam),
+ *   c = max over Gauss points of sqrt(u^2 + v^2) + sqrt(g h),
+ *   dt = cfl * H / (max(p, 1) * c),
+ * evaluated on the resident state on the GPU.  Returns DG_ENONPHYSICAL if
+ * h <= 0 at a Gauss point. */
+dg_status dg_max_dt(dg_handle h, double cfl, double *dt);
+
+/* Coordinates of the projection points: nm = p + 9 Gauss-Legendre points per
+ * element and direction.  lam receives nlon * nm values (index i * nm + q),
+ * theta nlat * nm values (index j * nm + q). */
+dg_status dg_projection_nodes(dg_handle h, double *lam, size_t nlam, double *theta, size_t ntheta);
+
+/* cos(theta)-weighted L^2 projection (mass matrix of Eq. ode) of point values
+ * onto the modal basis.  nodal holds the three fields at the projection
+ * points of every element, layout [j][i][f][q_theta][q_lambda]
+ * (len_nodal = nlat * nlon * 3 * nm * nm); modal_out receives dg_state_len(h)
+ * values.  Host computation in FP64; does not touch the resident state. */
+dg_status dg_project_nodal(dg_handle h, const double *nodal, size_t len_nodal, double *modal_out,
+                           size_t len);
+
+/* Simulated time of the resident state (advanced by dg_step). */
+dg_status dg_get_time(dg_handle h, double *t);
+dg_status dg_set_time(dg_handle h, double t);
+
+/* Number of fused stage-kernel launches issued by this handle so far. */
+long long dg_stage_launches(dg_handle h);
+
+/* Message describing the last failing call made by this thread (h may be
+ * NULL, e.g. after a failed dg_create); valid until the thread's next call.
+ * Never NULL. */
+const char *dg_last_error(dg_handle h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DGSWE_H */

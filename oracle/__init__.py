@@ -42,6 +42,8 @@ def lib():
         L.oracle_nm.argtypes = [ctypes.c_void_p]
         L.oracle_rhs.restype = ctypes.c_int
         L.oracle_rhs.argtypes = [ctypes.c_void_p, _dp, _dp]
+        L.oracle_rhs_magnitude.restype = ctypes.c_int
+        L.oracle_rhs_magnitude.argtypes = [ctypes.c_void_p, _dp, _dp]
         L.oracle_rhs_element.restype = ctypes.c_int
         L.oracle_rhs_element.argtypes = [ctypes.c_void_p, _dp, ctypes.c_int, ctypes.c_int, _dp]
         L.oracle_step.restype = ctypes.c_int
@@ -156,6 +158,16 @@ class Oracle:
         st = lib().oracle_rhs(self._h, _ptr(u), _ptr(out))
         if st:
             raise OracleError(f"rhs status {st}")
+        return out.reshape(self.shape)
+
+    def rhs_magnitude(self, u):
+        """|M^-1| sum |terms| of every tendency value: the scale of the rounding
+        error of any floating-point evaluation of the tendency."""
+        u = self._in(u)
+        out = np.empty_like(u)
+        st = lib().oracle_rhs_magnitude(self._h, _ptr(u), _ptr(out))
+        if st:
+            raise OracleError(f"rhs_magnitude status {st}")
         return out.reshape(self.shape)
 
     def rhs_element(self, u, j, i):

@@ -437,7 +437,24 @@ static void eval_point(const oracle_ctx *c, const double *modes, const double *p
  *     = int S phi
  * assembled in (x, y) = (lambda, theta) coordinates and multiplied by the
  * inverse element mass matrix of Eq. (ode).  out: nf * nphi values. */
+static int rhs_element_impl(const oracle_ctx *c, const double *u, int jy, int ix, double *out, int mag);
+
 int oracle_rhs_element(const oracle_ctx *c, const double *u, int jy, int ix, double *out)
+{
+    return rhs_element_impl(c, u, jy, ix, out, 0);
+}
+
+/* Magnitude bound of the tendency of element (jy, ix): the same assembly with
+ * every term replaced by its absolute value and the inverse mass matrix by its
+ * elementwise absolute value, |M^{-1}| sum |terms|.  Floating-point summation
+ * of the tendency errs by at most a small multiple of the unit roundoff times
+ * this bound, so it is the scale that tendency tolerances are taken against. */
+int oracle_rhs_magnitude_element(const oracle_ctx *c, const double *u, int jy, int ix, double *out)
+{
+    return rhs_element_impl(c, u, jy, ix, out, 1);
+}
+
+static int rhs_element_impl(const oracle_ctx *c, const double *u, int jy, int ix, double *out, int mag)
 {
     int n = c->n, np = c->nphi, nf = c->nf;
     double r[3 * 81];
@@ -458,7 +475,10 @@ int oracle_rhs_element(const oracle_ctx *c, const double *u, int jy, int ix, dou
                 double dpx = c->dphix[qi * np + m] * 2.0 / c->dx;
                 double dpy = c->dphiy[qi * np + m] * 2.0 / c->dy;
                 double ph = c->phiv[qi * np + m];
-                for (int f = 0; f < nf; ++f) r[f * np + m] += wq * (F[f] * dpx + G[f] * dpy + S[f] * ph);
+                for (int f = 0; f < nf; ++f) {
+                    if (mag) r[f * np + m] += fabs(wq * F[f] * dpx) + fabs(wq * G[f] * dpy) + fabs(wq * S[f] * ph);
+                    else r[f * np + m] += wq * (F[f] * dpx + G[f] * dpy + S[f] * ph);
+                }
             }
         }
 
@@ -494,7 +514,10 @@ int oracle_rhs_element(const oracle_ctx *c, const double *u, int jy, int ix, dou
             double we = c->wg[k] * ejac;
             for (int m = 0; m < np; ++m) {
                 double ph = phio[m];
-                for (int f = 0; f < nf; ++f) r[f * np + m] -= we * fn[f] * ph;
+                for (int f = 0; f < nf; ++f) {
+                    if (mag) r[f * np + m] += fabs(we * fn[f] * ph);
+                    else r[f * np + m] -= we * fn[f] * ph;
+                }
             }
         }
     }
@@ -504,14 +527,14 @@ int oracle_rhs_element(const oracle_ctx *c, const double *u, int jy, int ix, dou
     for (int f = 0; f < nf; ++f)
         for (int a = 0; a < np; ++a) {
             double acc = 0.0;
-            for (int b = 0; b < np; ++b) acc += mi[a * np + b] * r[f * np + b];
+            for (int b = 0; b < np; ++b)
+                acc += (mag ? fabs(mi[a * np + b]) : mi[a * np + b]) * r[f * np + b];
             out[f * np + a] = acc;
         }
     return ORACLE_OK;
 }
 
-/* du/dt = M^{-1} h(u) for every element (Eq. ode). */
-int oracle_rhs(const oracle_ctx *c, const double *u, double *tend)
+static int rhs_all(const oracle_ctx *c, const double *u, double *tend, int mag)
 {
     int status = ORACLE_OK;
     int nel = c->nx * c->ny;
@@ -520,10 +543,22 @@ int oracle_rhs(const oracle_ctx *c, const double *u, double *tend)
 #pragma omp parallel for schedule(static) num_threads(c->nthreads) reduction(max : status)
 #endif
     for (int e = 0; e < nel; ++e) {
-        int st = oracle_rhs_element(c, u, e / c->nx, e % c->nx, tend + (size_t)e * per);
+        int st = rhs_element_impl(c, u, e / c->nx, e % c->nx, tend + (size_t)e * per, mag);
         if (st > status) status = st;
     }
     return status;
+}
+
+/* du/dt = M^{-1} h(u) for every element (Eq. ode). */
+int oracle_rhs(const oracle_ctx *c, const double *u, double *tend)
+{
+    return rhs_all(c, u, tend, 0);
+}
+
+/* The magnitude bound of oracle_rhs_magnitude_element() for every element. */
+int oracle_rhs_magnitude(const oracle_ctx *c, const double *u, double *tend)
+{
+    return rhs_all(c, u, tend, 1);
 }
 
 /* ---------------------------------------------------------------- time -- */

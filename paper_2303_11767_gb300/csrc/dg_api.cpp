@@ -1,0 +1,821 @@
+// dg_api.cpp -- the C-ABI of libdgswe (declared in include/dgswe.h).
+//
+// The handle owns the FP64 host tables, the device buffers of the resident
+// state, the stream and the captured CUDA graphs of the Runge-Kutta steps.
+// Every time step is a fixed sequence of fused stage kernels (one per RK
+// stage, Table "Butcher" of the paper), captured once per (steps, dt, order,
+// precision) and replayed.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "dg_internal.h"
+#include "../../include/dgswe.h"
+
+namespace {
+
+thread_local std::string g_err;
+
+dg_status fail(dg_status s, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    std::vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return s;
+}
+
+#define CUDA_TRY(call)                                                                                       \
+    do {                                                                                                     \
+        cudaError_t e_ = (call);                                                                             \
+        if (e_ != cudaSuccess) return fail(DG_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_));       \
+    } while (0)
+
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) ok = cudaSetDevice(dev) == cudaSuccess;
+    }
+    ~DeviceGuard()
+    {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+struct GraphEntry {
+    cudaGraphExec_t exec = nullptr;
+    int steps = 0, order = 0, prec = 0, cur_in = 0, cur_out = 0;
+    double dt = 0;
+    cudaStream_t stream = nullptr;
+};
+
+unsigned long long g_basis_uploaded = 0;   // per-device bit: constant tables present
+
+}  // namespace
+
+struct dg_ctx {
+    int nlon = 0, nlat = 0, p = 0, n = 0, nphi = 0;
+    size_t nel = 0, len = 0;
+    double R = 0, g = 0, omega = 0;
+    int device = 0;
+    HostTables tab;
+    // options
+    int prec = DG_PREC_FP64, rk = 3, check = 1, alpha_mode = 0, spg = 16;
+    cudaStream_t own_stream = nullptr, stream = nullptr;
+    // device buffers
+    void *U[4] = {nullptr, nullptr, nullptr, nullptr};   // state buffers of the active precision
+    int cur = 0;                                          // buffer holding the state
+    double *stage64 = nullptr;                            // FP64 staging of one state
+    RowTab<double> *rows64 = nullptr;
+    RowTab<float> *rows32 = nullptr;
+    double *c0 = nullptr;                                 // mass table: C_j[0][b], then row areas
+    double *partials = nullptr;                           // per-block compensated mass sums
+    int nblocks = 0;
+    double *d_result = nullptr;
+    unsigned *d_status = nullptr;
+    unsigned long long *d_maxbits = nullptr;
+    double href = 0;      // reference depth of the resident state (FP32 path); 0 for FP64
+    double t = 0;
+    bool have_state = false;
+    long long launches = 0;       // fused stage kernels
+    long long aux_launches = 0;   // conversion, mass and wave-speed kernels
+    std::vector<GraphEntry> graphs;
+};
+
+namespace {
+
+size_t elem_size(int prec) { return prec == DG_PREC_FP64 ? sizeof(double) : sizeof(float); }
+
+void drop_graphs(dg_ctx *h)
+{
+    for (auto &g : h->graphs)
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+    h->graphs.clear();
+}
+
+void free_state_buffers(dg_ctx *h)
+{
+    for (auto &u : h->U) {
+        if (u) cudaFree(u);
+        u = nullptr;
+    }
+}
+
+dg_status alloc_state_buffers(dg_ctx *h)
+{
+    const size_t bytes = h->len * elem_size(h->prec);
+    for (auto &u : h->U) {
+        if (cudaMalloc(&u, bytes) != cudaSuccess) {
+            free_state_buffers(h);
+            return fail(DG_ENOMEM, "cudaMalloc of %zu bytes failed", bytes);
+        }
+    }
+    return DG_OK;
+}
+
+// Stage launch in the active precision.
+template <typename T>
+StageArgs<T> base_args(dg_ctx *h, const RowTab<T> *rows, double href)
+{
+    StageArgs<T> a;
+    std::memset(&a, 0, sizeof a);
+    a.rows = rows;
+    a.status = h->d_status;
+    a.nlon = h->nlon;
+    a.nlat = h->nlat;
+    a.href = (T)href;
+    a.P0 = (T)(0.5 * h->g * href * href);
+    a.g = (T)h->g;
+    a.cF = (T)(2.0 / (h->R * h->tab.dlam));
+    a.cG = (T)(2.0 / (h->R * h->tab.dth));
+    a.invR = (T)(1.0 / h->R);
+    a.twoOmega = (T)(2.0 * h->omega);
+    return a;
+}
+
+struct StagePlan {
+    int in, P, out, P2, out2;   // buffer indices, -1 = none
+    double ca, cb, cc, ca2, cc2;
+};
+
+// The explicit RK schemes of Table "Butcher" in low-storage form.  Buffer
+// indices are relative: 0 is the buffer holding u^n.
+int rk_plan(int order, StagePlan *pl, int *flips)
+{
+    *flips = 0;
+    switch (order) {
+    case 1:   // u1 = u + dt k(u); the result lives in the other buffer
+        pl[0] = {0, -1, 1, -1, -1, 0, 1, 1, 0, 0};
+        *flips = 1;
+        return 1;
+    case 2:   // u1 = u + dt k(u); u = u/2 + (u1 + dt k(u1))/2
+        pl[0] = {0, -1, 1, -1, -1, 0, 1, 1, 0, 0};
+        pl[1] = {1, 0, 0, -1, -1, 0.5, 0.5, 0.5, 0, 0};
+        return 2;
+    case 3:   // Shu-Osher form of the SSP RK3 tableau
+        pl[0] = {0, -1, 1, -1, -1, 0, 1, 1, 0, 0};
+        pl[1] = {1, 0, 2, -1, -1, 0.75, 0.25, 0.25, 0, 0};
+        pl[2] = {2, 0, 0, -1, -1, 1.0 / 3.0, 2.0 / 3.0, 2.0 / 3.0, 0, 0};
+        return 3;
+    case 4:   // classical RK4 tableau with an accumulator (buffer 3)
+        pl[0] = {0, -1, 1, 0, 3, 0, 1, 0.5, 1, 1.0 / 6.0};
+        pl[1] = {1, 0, 2, 3, 3, 1, 0, 0.5, 1, 1.0 / 3.0};
+        pl[2] = {2, 0, 1, 3, 3, 1, 0, 1.0, 1, 1.0 / 3.0};
+        pl[3] = {1, 3, 0, -1, -1, 1, 0, 1.0 / 6.0, 0, 0};
+        return 4;
+    default:
+        return 0;
+    }
+}
+
+template <typename T>
+dg_status launch_step_t(dg_ctx *h, double dt, int cur, const RowTab<T> *rows)
+{
+    StagePlan pl[4];
+    int flips = 0;
+    const int ns = rk_plan(h->rk, pl, &flips);
+    auto buf = [&](int rel) -> T * {
+        if (rel < 0) return nullptr;
+        int idx = rel;
+        if (rel <= 1) idx = rel ^ cur;   // buffers 0 and 1 swap roles for RK1 ping-pong
+        return static_cast<T *>(h->U[idx]);
+    };
+    for (int s = 0; s < ns; ++s) {
+        StageArgs<T> a = base_args<T>(h, rows, h->href);
+        a.u_in = buf(pl[s].in);
+        a.P = buf(pl[s].P);
+        a.out = buf(pl[s].out);
+        a.P2 = buf(pl[s].P2);
+        a.out2 = buf(pl[s].out2);
+        a.ca = (T)pl[s].ca;
+        a.cb = (T)pl[s].cb;
+        a.cc = (T)pl[s].cc;
+        a.ca2 = (T)pl[s].ca2;
+        a.cc2 = (T)pl[s].cc2;
+        a.dt = (T)dt;
+        if (dg_launch_stage<T>(h->n, a, h->stream))
+            return fail(DG_ECUDA, "stage kernel launch failed: %s", cudaGetErrorString(cudaGetLastError()));
+        h->launches++;
+    }
+    return DG_OK;
+}
+
+dg_status launch_steps(dg_ctx *h, int nsteps, double dt, int *cur)
+{
+    for (int s = 0; s < nsteps; ++s) {
+        dg_status st = h->prec == DG_PREC_FP64 ? launch_step_t<double>(h, dt, *cur, h->rows64)
+                                               : launch_step_t<float>(h, dt, *cur, h->rows32);
+        if (st) return st;
+        if (h->rk == 1) *cur ^= 1;
+    }
+    return DG_OK;
+}
+
+dg_status read_status(dg_ctx *h)
+{
+    unsigned st = 0;
+    CUDA_TRY(cudaMemcpyAsync(&st, h->d_status, sizeof st, cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
+    if (st) {
+        CUDA_TRY(cudaMemsetAsync(h->d_status, 0, sizeof(unsigned), h->stream));
+        if (st & DG_STATUS_NONPHYSICAL) return fail(DG_ENONPHYSICAL, "h <= 0 at a quadrature point");
+        return fail(DG_ENONFINITE, "non-finite value in the state");
+    }
+    return DG_OK;
+}
+
+dg_status check(dg_ctx *h)
+{
+    if (!h) return fail(DG_EINVAL, "NULL handle");
+    return DG_OK;
+}
+
+template <typename T>
+dg_status upload_rows(dg_ctx *h, RowTab<T> **dst)
+{
+    std::vector<RowTab<T>> r(h->nlat);
+    for (int j = 0; j < h->nlat; ++j) {
+        const RowTab<double> &s = h->tab.rows[j];
+        RowTab<T> &d = r[j];
+        std::memset(&d, 0, sizeof d);
+        for (int a = 0; a < DG_MAXN; ++a) {
+            d.cosn[a] = (T)s.cosn[a];
+            d.sinn[a] = (T)s.sinn[a];
+            d.rho[a] = (T)s.rho[a];
+            for (int b = 0; b < DG_MAXN; ++b) {
+                d.Ci[a][b] = (T)s.Ci[a][b];
+                d.Q[a][b] = (T)s.Q[a][b];
+            }
+        }
+        d.ce_s = (T)s.ce_s;
+        d.ce_n = (T)s.ce_n;
+    }
+    const size_t bytes = sizeof(RowTab<T>) * h->nlat;
+    if (cudaMalloc(reinterpret_cast<void **>(dst), bytes) != cudaSuccess)
+        return fail(DG_ENOMEM, "cudaMalloc of row tables failed");
+    CUDA_TRY(cudaMemcpy(*dst, r.data(), bytes, cudaMemcpyHostToDevice));
+    return DG_OK;
+}
+
+dg_status upload_basis_once(int dev)
+{
+    if (g_basis_uploaded >> dev & 1ull) return DG_OK;
+    BasisTab<double> all[DG_MAXN];
+    for (int n = 1; n <= DG_MAXN; ++n) {
+        HostTables t;
+        if (dg_build_tables(t, 1, 2, n - 1, 1.0, 1.0)) {
+            dg_free_tables(t);
+            return fail(DG_EINVAL, "basis table construction failed");
+        }
+        all[n - 1] = t.basis;
+        dg_free_tables(t);
+    }
+    if (dg_upload_basis<float>(all) || dg_upload_basis<double>(all))
+        return fail(DG_ECUDA, "upload of the basis tables failed: %s", cudaGetErrorString(cudaGetLastError()));
+    g_basis_uploaded |= 1ull << dev;
+    return DG_OK;
+}
+
+double mean_depth(const double *modal, size_t nel, int nphi)
+{
+    double s = 0.0;
+    for (size_t e = 0; e < nel; ++e) s += modal[e * 3 * nphi];
+    return 0.5 * s / (double)nel;   // mode 0 of h times phi_0 = 1/2
+}
+
+dg_status to_internal(dg_ctx *h, const double *d_src, void *dst, double href)
+{
+    int r = h->prec == DG_PREC_FP64
+                ? dg_launch_to_internal<double>(d_src, static_cast<double *>(dst), h->nel, h->nphi, href, h->stream)
+                : dg_launch_to_internal<float>(d_src, static_cast<float *>(dst), h->nel, h->nphi, href, h->stream);
+    if (r) return fail(DG_ECUDA, "conversion kernel failed: %s", cudaGetErrorString(cudaGetLastError()));
+    return DG_OK;
+}
+
+dg_status to_api(dg_ctx *h, const void *src, double *d_dst, double href)
+{
+    int r = h->prec == DG_PREC_FP64
+                ? dg_launch_to_api<double>(static_cast<const double *>(src), d_dst, h->nel, h->nphi, href, h->stream)
+                : dg_launch_to_api<float>(static_cast<const float *>(src), d_dst, h->nel, h->nphi, href, h->stream);
+    if (r) return fail(DG_ECUDA, "conversion kernel failed: %s", cudaGetErrorString(cudaGetLastError()));
+    return DG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+dg_status dg_set_device(int device)
+{
+    int count = 0;
+    if (cudaGetDeviceCount(&count) != cudaSuccess) return fail(DG_ECUDA, "no CUDA device");
+    if (device < 0 || device >= count) return fail(DG_EINVAL, "device %d of %d", device, count);
+    CUDA_TRY(cudaSetDevice(device));
+    return DG_OK;
+}
+
+dg_status dg_create(int nlon, int nlat, int degree, double radius, double g, double omega, dg_handle *out)
+{
+    if (!out) return fail(DG_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (nlon < 1 || nlat < 2) return fail(DG_EINVAL, "need nlon >= 1 and nlat >= 2 (got %d, %d)", nlon, nlat);
+    if (degree < 0 || degree > DG_MAXN - 1) return fail(DG_EINVAL, "degree must be in [0, %d]", DG_MAXN - 1);
+    if (!(radius > 0) || !(g > 0) || !std::isfinite(omega))
+        return fail(DG_EINVAL, "radius and g must be positive, omega finite");
+    if ((double)nlon * nlat > 2.0e9) return fail(DG_EINVAL, "mesh too large");
+    dg_ctx *h = new (std::nothrow) dg_ctx;
+    if (!h) return fail(DG_ENOMEM, "host allocation failed");
+    h->nlon = nlon;
+    h->nlat = nlat;
+    h->p = degree;
+    h->n = degree + 1;
+    h->nphi = h->n * h->n;
+    h->nel = (size_t)nlon * nlat;
+    h->len = h->nel * 3 * h->nphi;
+    h->R = radius;
+    h->g = g;
+    h->omega = omega;
+    dg_status st = DG_OK;
+    if (cudaGetDevice(&h->device) != cudaSuccess) {
+        delete h;
+        return fail(DG_ECUDA, "no CUDA device: %s", cudaGetErrorString(cudaGetLastError()));
+    }
+    if (dg_build_tables(h->tab, nlon, nlat, degree, radius, g)) {
+        dg_free_tables(h->tab);
+        delete h;
+        return fail(DG_EINVAL, "table construction failed");
+    }
+#define CREATE_TRY(x)                 \
+    do {                              \
+        st = (x);                     \
+        if (st) {                     \
+            dg_destroy(h);            \
+            return st;                \
+        }                             \
+    } while (0)
+    CREATE_TRY(upload_basis_once(h->device));
+    if (cudaStreamCreateWithFlags(&h->own_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        dg_destroy(h);
+        return fail(DG_ECUDA, "stream creation failed");
+    }
+    h->stream = h->own_stream;
+    CREATE_TRY(alloc_state_buffers(h));
+    if (cudaMalloc(&h->stage64, h->len * sizeof(double)) != cudaSuccess) {
+        dg_destroy(h);
+        return fail(DG_ENOMEM, "cudaMalloc of the staging buffer failed");
+    }
+    CREATE_TRY(upload_rows<double>(h, &h->rows64));
+    CREATE_TRY(upload_rows<float>(h, &h->rows32));
+    {
+        std::vector<double> c0((size_t)nlat * h->n + nlat);
+        for (int j = 0; j < nlat; ++j) {
+            for (int b = 0; b < h->n; ++b) c0[(size_t)j * h->n + b] = h->tab.C[(size_t)j * h->nphi + b];
+            const double tb = -0.5 * M_PI + j * h->tab.dth;
+            c0[(size_t)nlat * h->n + j] = std::sin(tb + h->tab.dth) - std::sin(tb);
+        }
+        if (cudaMalloc(&h->c0, c0.size() * sizeof(double)) != cudaSuccess) {
+            dg_destroy(h);
+            return fail(DG_ENOMEM, "cudaMalloc failed");
+        }
+        if (cudaMemcpy(h->c0, c0.data(), c0.size() * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess) {
+            dg_destroy(h);
+            return fail(DG_ECUDA, "copy of the mass table failed");
+        }
+    }
+    h->nblocks = dg_mass_blocks(h->nel);
+    if (cudaMalloc(&h->partials, 2 * sizeof(double) * h->nblocks) != cudaSuccess ||
+        cudaMalloc(&h->d_result, sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&h->d_status, sizeof(unsigned)) != cudaSuccess ||
+        cudaMalloc(&h->d_maxbits, sizeof(unsigned long long)) != cudaSuccess) {
+        dg_destroy(h);
+        return fail(DG_ENOMEM, "cudaMalloc failed");
+    }
+    if (cudaMemset(h->d_status, 0, sizeof(unsigned)) != cudaSuccess) {
+        dg_destroy(h);
+        return fail(DG_ECUDA, "cudaMemset failed");
+    }
+#undef CREATE_TRY
+    *out = h;
+    return DG_OK;
+}
+
+dg_status dg_destroy(dg_handle h)
+{
+    if (!h) return DG_OK;
+    DeviceGuard dg(h->device);
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    drop_graphs(h);
+    free_state_buffers(h);
+    cudaFree(h->stage64);
+    cudaFree(h->rows64);
+    cudaFree(h->rows32);
+    cudaFree(h->c0);
+    cudaFree(h->partials);
+    cudaFree(h->d_result);
+    cudaFree(h->d_status);
+    cudaFree(h->d_maxbits);
+    if (h->own_stream) cudaStreamDestroy(h->own_stream);
+    dg_free_tables(h->tab);
+    delete h;
+    return DG_OK;
+}
+
+size_t dg_state_len(dg_handle h) { return h ? h->len : 0; }
+
+long long dg_stage_launches(dg_handle h) { return h ? h->launches : 0; }
+
+const char *dg_last_error(dg_handle) { return g_err.c_str(); }
+
+dg_status dg_set_option(dg_handle h, int key, long long value)
+{
+    if (dg_status s = check(h)) return s;
+    DeviceGuard dg(h->device);
+    switch (key) {
+    case DG_OPT_PRECISION: {
+        if (value == DG_PREC_FP32_TC_BF16 || value == DG_PREC_FP32_TC_FP16)
+            return fail(DG_EUNSUPPORTED, "tensor-core precision %lld is not built", value);
+        if (value != DG_PREC_FP64 && value != DG_PREC_FP32) return fail(DG_EINVAL, "unknown precision %lld", value);
+        if (value == h->prec) return DG_OK;
+        CUDA_TRY(cudaStreamSynchronize(h->stream));
+        // carry the resident state over through the FP64 staging buffer
+        if (h->have_state) {
+            if (dg_status s = to_api(h, h->U[h->cur], h->stage64, h->href)) return s;
+            CUDA_TRY(cudaStreamSynchronize(h->stream));
+        }
+        drop_graphs(h);
+        free_state_buffers(h);
+        h->prec = (int)value;
+        if (dg_status s = alloc_state_buffers(h)) return s;
+        h->cur = 0;
+        if (h->have_state) {
+            if (h->prec == DG_PREC_FP32) {
+                // reference depth: mean of the element mean depths
+                std::vector<double> m0(h->nel);
+                CUDA_TRY(cudaMemcpy2D(m0.data(), sizeof(double), h->stage64, sizeof(double) * 3 * h->nphi,
+                                      sizeof(double), h->nel, cudaMemcpyDeviceToHost));
+                double s = 0;
+                for (double v : m0) s += v;
+                h->href = 0.5 * s / (double)h->nel;
+            } else {
+                h->href = 0.0;
+            }
+            if (dg_status s = to_internal(h, h->stage64, h->U[0], h->href)) return s;
+            CUDA_TRY(cudaStreamSynchronize(h->stream));
+        }
+        return DG_OK;
+    }
+    case DG_OPT_RK_ORDER:
+        if (value < 1 || value > 4) return fail(DG_EINVAL, "RK order must be 1..4");
+        h->rk = (int)value;
+        return DG_OK;
+    case DG_OPT_CHECK_FINITE:
+        h->check = value ? 1 : 0;
+        return DG_OK;
+    case DG_OPT_ALPHA_MODE:
+        if (value == 0) {
+            h->alpha_mode = 0;
+            return DG_OK;
+        }
+        if (value == 1) return fail(DG_EUNSUPPORTED, "global Rusanov alpha is not built");
+        return fail(DG_EINVAL, "unknown alpha mode %lld", value);
+    case DG_OPT_STREAM:
+        CUDA_TRY(cudaStreamSynchronize(h->stream));
+        h->stream = value ? reinterpret_cast<cudaStream_t>(value) : h->own_stream;
+        drop_graphs(h);
+        return DG_OK;
+    case DG_OPT_STEPS_PER_GRAPH:
+        if (value < 1 || value > 1024) return fail(DG_EINVAL, "steps per graph must be 1..1024");
+        h->spg = (int)value;
+        return DG_OK;
+    default:
+        return fail(DG_EINVAL, "unknown option %d", key);
+    }
+}
+
+dg_status dg_set_state_device(dg_handle h, const double *d_modal, size_t len)
+{
+    if (dg_status s = check(h)) return s;
+    if (!d_modal || len != h->len) return fail(DG_EINVAL, "state length %zu, expected %zu", len, h->len);
+    DeviceGuard dg(h->device);
+    CUDA_TRY(cudaMemcpyAsync(h->stage64, d_modal, len * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+    h->href = 0.0;
+    if (h->prec == DG_PREC_FP32) {
+        std::vector<double> m0(h->nel);
+        CUDA_TRY(cudaMemcpy2DAsync(m0.data(), sizeof(double), h->stage64, sizeof(double) * 3 * h->nphi,
+                                   sizeof(double), h->nel, cudaMemcpyDeviceToHost, h->stream));
+        CUDA_TRY(cudaStreamSynchronize(h->stream));
+        double s = 0;
+        for (double v : m0) s += v;
+        h->href = 0.5 * s / (double)h->nel;
+    }
+    h->cur = 0;
+    if (dg_status s = to_internal(h, h->stage64, h->U[0], h->href)) return s;
+    h->have_state = true;
+    return DG_OK;
+}
+
+dg_status dg_set_state(dg_handle h, const double *modal, size_t len)
+{
+    if (dg_status s = check(h)) return s;
+    if (!modal || len != h->len) return fail(DG_EINVAL, "state length %zu, expected %zu", len, h->len);
+    DeviceGuard dg(h->device);
+    CUDA_TRY(cudaMemcpyAsync(h->stage64, modal, len * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    h->href = h->prec == DG_PREC_FP32 ? mean_depth(modal, h->nel, h->nphi) : 0.0;
+    h->cur = 0;
+    if (dg_status s = to_internal(h, h->stage64, h->U[0], h->href)) return s;
+    CUDA_TRY(cudaStreamSynchronize(h->stream));   // the host buffer is only borrowed
+    h->have_state = true;
+    return DG_OK;
+}
+
+dg_status dg_get_state_device(dg_handle h, double *d_modal, size_t len)
+{
+    if (dg_status s = check(h)) return s;
+    if (!d_modal || len != h->len) return fail(DG_EINVAL, "state length %zu, expected %zu", len, h->len);
+    if (!h->have_state) return fail(DG_EINVAL, "no state set");
+    DeviceGuard dg(h->device);
+    return to_api(h, h->U[h->cur], d_modal, h->href);
+}
+
+dg_status dg_get_state(dg_handle h, double *modal, size_t len)
+{
+    if (dg_status s = check(h)) return s;
+    if (!modal || len != h->len) return fail(DG_EINVAL, "state length %zu, expected %zu", len, h->len);
+    if (!h->have_state) return fail(DG_EINVAL, "no state set");
+    DeviceGuard dg(h->device);
+    if (dg_status s = to_api(h, h->U[h->cur], h->stage64, h->href)) return s;
+    CUDA_TRY(cudaMemcpyAsync(modal, h->stage64, len * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
+    return DG_OK;
+}
+
+dg_status dg_rhs(dg_handle h, const double *modal_in, double *tend_out, size_t len)
+{
+    if (dg_status s = check(h)) return s;
+    if (!modal_in || !tend_out || len != h->len) return fail(DG_EINVAL, "state length %zu, expected %zu", len, h->len);
+    DeviceGuard dg(h->device);
+    // scratch: every buffer but U[cur] is free between steps (cur is 0 or 1)
+    void *in = h->U[h->cur ^ 1], *outb = h->U[2];
+    const double href = h->prec == DG_PREC_FP32 ? mean_depth(modal_in, h->nel, h->nphi) : 0.0;
+    CUDA_TRY(cudaMemcpyAsync(h->stage64, modal_in, len * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    if (dg_status s = to_internal(h, h->stage64, in, href)) return s;
+    int r;
+    if (h->prec == DG_PREC_FP64) {
+        StageArgs<double> a = base_args<double>(h, h->rows64, href);
+        a.u_in = static_cast<double *>(in);
+        a.out = static_cast<double *>(outb);
+        a.cc = 1.0;
+        a.dt = 1.0;
+        r = dg_launch_stage<double>(h->n, a, h->stream);
+    } else {
+        StageArgs<float> a = base_args<float>(h, h->rows32, href);
+        a.u_in = static_cast<float *>(in);
+        a.out = static_cast<float *>(outb);
+        a.cc = 1.0f;
+        a.dt = 1.0f;
+        r = dg_launch_stage<float>(h->n, a, h->stream);
+    }
+    if (r) return fail(DG_ECUDA, "stage kernel launch failed: %s", cudaGetErrorString(cudaGetLastError()));
+    h->launches++;
+    if (dg_status s = to_api(h, outb, h->stage64, 0.0)) return s;   // tendencies carry no reference depth
+    CUDA_TRY(cudaMemcpyAsync(tend_out, h->stage64, len * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
+    if (h->check) return read_status(h);
+    return DG_OK;
+}
+
+dg_status dg_step(dg_handle h, int n, double dt)
+{
+    if (dg_status s = check(h)) return s;
+    if (n < 0) return fail(DG_EINVAL, "n must be >= 0");
+    if (!(dt > 0) || !std::isfinite(dt)) return fail(DG_EINVAL, "dt must be positive and finite");
+    if (!h->have_state) return fail(DG_EINVAL, "no state set");
+    if (n == 0) return DG_OK;
+    DeviceGuard dg(h->device);
+    int K = std::min(h->spg, n);
+    if (h->rk == 1 && (K & 1) && K > 1) K -= 1;   // keep the ping-pong even inside a graph
+    int full = n / K, rest = n - full * K;
+    if (full > 0) {
+        GraphEntry *ge = nullptr;
+        for (auto &g : h->graphs)
+            if (g.steps == K && g.dt == dt && g.order == h->rk && g.prec == h->prec && g.cur_in == h->cur &&
+                g.stream == h->stream)
+                ge = &g;
+        if (!ge) {
+            GraphEntry g;
+            g.steps = K;
+            g.dt = dt;
+            g.order = h->rk;
+            g.prec = h->prec;
+            g.cur_in = h->cur;
+            g.stream = h->stream;
+            int cur = h->cur;
+            long long before = h->launches;
+            CUDA_TRY(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+            dg_status st = launch_steps(h, K, dt, &cur);
+            cudaGraph_t graph = nullptr;
+            cudaError_t ce = cudaStreamEndCapture(h->stream, &graph);
+            h->launches = before;   // capture only records; replays are counted below
+            if (st) {
+                if (graph) cudaGraphDestroy(graph);
+                return st;
+            }
+            if (ce != cudaSuccess) return fail(DG_ECUDA, "graph capture failed: %s", cudaGetErrorString(ce));
+            ce = cudaGraphInstantiate(&g.exec, graph, 0);
+            cudaGraphDestroy(graph);
+            if (ce != cudaSuccess) return fail(DG_ECUDA, "graph instantiation failed: %s", cudaGetErrorString(ce));
+            g.cur_out = cur;
+            if (h->graphs.size() >= 8) {
+                cudaGraphExecDestroy(h->graphs.front().exec);
+                h->graphs.erase(h->graphs.begin());
+            }
+            h->graphs.push_back(g);
+            ge = &h->graphs.back();
+        }
+        StagePlan pl[4];
+        int flips;
+        const int ns = rk_plan(h->rk, pl, &flips);
+        for (int r = 0; r < full; ++r) {
+            CUDA_TRY(cudaGraphLaunch(ge->exec, h->stream));
+            h->launches += (long long)K * ns;
+            h->cur = ge->cur_out;
+        }
+    }
+    if (rest > 0) {
+        int cur = h->cur;
+        if (dg_status st = launch_steps(h, rest, dt, &cur)) return st;
+        h->cur = cur;
+    }
+    h->t += n * dt;
+    if (h->check) return read_status(h);
+    return DG_OK;
+}
+
+}  // extern "C"
+
+namespace {
+dg_status enqueue_mass(dg_ctx *h, double *d_out)
+{
+    int r = h->prec == DG_PREC_FP64
+                ? dg_launch_mass<double>(static_cast<const double *>(h->U[h->cur]), h->c0, h->nlon, h->nlat, h->n,
+                                         h->href, h->tab.dlam, h->tab.dth, h->R * h->R, h->partials, h->nblocks,
+                                         d_out, h->stream)
+                : dg_launch_mass<float>(static_cast<const float *>(h->U[h->cur]), h->c0, h->nlon, h->nlat, h->n,
+                                        h->href, h->tab.dlam, h->tab.dth, h->R * h->R, h->partials, h->nblocks,
+                                        d_out, h->stream);
+    if (r) return fail(DG_ECUDA, "mass kernel failed: %s", cudaGetErrorString(cudaGetLastError()));
+    h->aux_launches += 2;
+    return DG_OK;
+}
+}  // namespace
+
+extern "C" {
+
+dg_status dg_total_mass(dg_handle h, double *mass)
+{
+    if (dg_status s = check(h)) return s;
+    if (!mass) return fail(DG_EINVAL, "mass is NULL");
+    if (!h->have_state) return fail(DG_EINVAL, "no state set");
+    DeviceGuard dg(h->device);
+    if (dg_status s = enqueue_mass(h, h->d_result)) return s;
+    double m = 0;
+    CUDA_TRY(cudaMemcpyAsync(&m, h->d_result, sizeof m, cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
+    *mass = m;
+    return DG_OK;
+}
+
+dg_status dg_total_mass_device(dg_handle h, double *d_mass)
+{
+    if (dg_status s = check(h)) return s;
+    if (!d_mass) return fail(DG_EINVAL, "d_mass is NULL");
+    if (!h->have_state) return fail(DG_EINVAL, "no state set");
+    DeviceGuard dg(h->device);
+    return enqueue_mass(h, d_mass);
+}
+
+dg_status dg_max_dt(dg_handle h, double cfl, double *dt)
+{
+    if (dg_status s = check(h)) return s;
+    if (!dt || !(cfl > 0)) return fail(DG_EINVAL, "need cfl > 0 and dt != NULL");
+    if (!h->have_state) return fail(DG_EINVAL, "no state set");
+    DeviceGuard dg(h->device);
+    CUDA_TRY(cudaMemsetAsync(h->d_maxbits, 0, sizeof(unsigned long long), h->stream));
+    int r = h->prec == DG_PREC_FP64
+                ? dg_launch_max_speed<double>(static_cast<const double *>(h->U[h->cur]), h->nlon, h->nlat, h->n,
+                                              h->href, h->g, h->d_maxbits, h->d_status, h->stream)
+                : dg_launch_max_speed<float>(static_cast<const float *>(h->U[h->cur]), h->nlon, h->nlat, h->n,
+                                             h->href, h->g, h->d_maxbits, h->d_status, h->stream);
+    if (r) return fail(DG_ECUDA, "wave-speed kernel failed: %s", cudaGetErrorString(cudaGetLastError()));
+    unsigned long long bits = 0;
+    CUDA_TRY(cudaMemcpyAsync(&bits, h->d_maxbits, sizeof bits, cudaMemcpyDeviceToHost, h->stream));
+    if (dg_status s = read_status(h)) return s;
+    double c;
+    std::memcpy(&c, &bits, sizeof c);
+    if (!(c > 0)) return fail(DG_ENONPHYSICAL, "no positive wave speed");
+    double H = INFINITY;
+    for (int j = 0; j < h->nlat; ++j)
+        for (int q = 0; q < h->n; ++q)
+            H = std::min(H, std::min(h->R * h->tab.dth, h->R * h->tab.rows[j].cosn[q] * h->tab.dlam));
+    *dt = cfl * H / (std::max(h->p, 1) * c);
+    return DG_OK;
+}
+
+dg_status dg_projection_nodes(dg_handle h, double *lam, size_t nlam, double *theta, size_t ntheta)
+{
+    if (dg_status s = check(h)) return s;
+    const int nm = h->tab.nm;
+    if (!lam || !theta || nlam != (size_t)h->nlon * nm || ntheta != (size_t)h->nlat * nm)
+        return fail(DG_EINVAL, "need nlon*nm = %zu and nlat*nm = %zu values", (size_t)h->nlon * nm,
+                    (size_t)h->nlat * nm);
+    for (int i = 0; i < h->nlon; ++i)
+        for (int q = 0; q < nm; ++q) lam[(size_t)i * nm + q] = (i + 0.5 * (1.0 + h->tab.xm[q])) * h->tab.dlam;
+    for (int j = 0; j < h->nlat; ++j)
+        for (int q = 0; q < nm; ++q)
+            theta[(size_t)j * nm + q] = -0.5 * M_PI + (j + 0.5 * (1.0 + h->tab.xm[q])) * h->tab.dth;
+    return DG_OK;
+}
+
+dg_status dg_project_nodal(dg_handle h, const double *nodal, size_t len_nodal, double *modal_out, size_t len)
+{
+    if (dg_status s = check(h)) return s;
+    const int n = h->n, nm = h->tab.nm;
+    if (!nodal || !modal_out || len != h->len || len_nodal != h->nel * 3 * nm * nm)
+        return fail(DG_EINVAL, "bad lengths");
+    // separable projection: sum over the lambda points, then the theta points
+    // weighted by cos(theta), then the inverse of C_j (the dlam dth / 4 of the
+    // mass matrix cancels against the same factor of the right-hand side)
+    std::vector<double> PL((size_t)n * nm), PC((size_t)n * nm), s((size_t)nm * n), r((size_t)n * n);
+    for (int a = 0; a < n; ++a)
+        for (int q = 0; q < nm; ++q) PL[(size_t)a * nm + q] = h->tab.wm[q] * dg_legendre(a, h->tab.xm[q]);
+    for (int j = 0; j < h->nlat; ++j) {
+        const double tb = -0.5 * M_PI + j * h->tab.dth;
+        for (int b = 0; b < n; ++b)
+            for (int q = 0; q < nm; ++q)
+                PC[(size_t)b * nm + q] =
+                    PL[(size_t)b * nm + q] * std::cos(tb + 0.5 * (1.0 + h->tab.xm[q]) * h->tab.dth);
+        const RowTab<double> &rt = h->tab.rows[j];
+        for (int i = 0; i < h->nlon; ++i)
+            for (int f = 0; f < 3; ++f) {
+                const size_t el = (size_t)j * h->nlon + i;
+                const double *v = nodal + (el * 3 + f) * nm * nm;
+                for (int qy = 0; qy < nm; ++qy)
+                    for (int a = 0; a < n; ++a) {
+                        double acc = 0;
+                        for (int qx = 0; qx < nm; ++qx) acc += PL[(size_t)a * nm + qx] * v[qy * nm + qx];
+                        s[(size_t)qy * n + a] = acc;
+                    }
+                for (int b = 0; b < n; ++b)
+                    for (int a = 0; a < n; ++a) {
+                        double acc = 0;
+                        for (int qy = 0; qy < nm; ++qy) acc += PC[(size_t)b * nm + qy] * s[(size_t)qy * n + a];
+                        r[(size_t)b * n + a] = acc;
+                    }
+                double *o = modal_out + (el * 3 + f) * h->nphi;
+                for (int b = 0; b < n; ++b)
+                    for (int a = 0; a < n; ++a) {
+                        double acc = 0;
+                        for (int c = 0; c < n; ++c) acc += rt.Ci[b][c] * r[(size_t)c * n + a];
+                        o[b * n + a] = acc;
+                    }
+            }
+    }
+    return DG_OK;
+}
+
+dg_status dg_get_time(dg_handle h, double *t)
+{
+    if (dg_status s = check(h)) return s;
+    if (!t) return fail(DG_EINVAL, "t is NULL");
+    *t = h->t;
+    return DG_OK;
+}
+
+dg_status dg_set_time(dg_handle h, double t)
+{
+    if (dg_status s = check(h)) return s;
+    if (!std::isfinite(t)) return fail(DG_EINVAL, "t must be finite");
+    h->t = t;
+    return DG_OK;
+}
+
+}  // extern "C"
+
+int dg_mass_blocks(size_t nel)
+{
+    size_t b = (nel + 1023) / 1024;
+    return (int)std::max<size_t>(1, std::min<size_t>(b, 1024));
+}

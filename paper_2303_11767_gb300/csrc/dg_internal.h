@@ -1,0 +1,97 @@
+// dg_internal.h -- types shared by the translation units of libdgswe.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#define DG_MAXN 5          // up to degree 4: (p+1) <= 5 modes per direction
+#define DG_WARPS 8         // warps per stage-kernel block (= tile rows)
+
+// Basis tables of one n = p+1 (n Gauss-Legendre points xi on [-1, 1]):
+//   LV[a][q]  = L_a(xi_q)             SE[a] = L_a(+1)      SW[a] = L_a(-1)
+//   WLV[a][q] = w_q L_a(xi_q)         WLD[a][q] = w_q L_a'(xi_q)
+template <typename T>
+struct BasisTab {
+    T LV[DG_MAXN][DG_MAXN];
+    T WLV[DG_MAXN][DG_MAXN];
+    T WLD[DG_MAXN][DG_MAXN];
+    T SE[DG_MAXN];
+    T SW[DG_MAXN];
+};
+
+// Per latitude row j (the element mass matrix depends only on the row):
+//   cosn/sinn: cos, sin of theta at the n Gauss points of the row
+//   ce_s/ce_n: cos(theta) at the south / north edge (0 at a pole edge)
+//   Ci:  inverse of C_j[b][b'] = int L_b L_b' cos(theta(eta)) deta
+//   Q:   Ci * WLV, i.e. Q[b][q] = sum_b' Ci[b][b'] w_q L_b'(eta_q)
+//   rho: hv tendency of the (a = 0, b) modes produced by a unit constant
+//        pressure flux (the rest state with g h^2 / 2 = 1), n-point rules
+template <typename T>
+struct RowTab {
+    T cosn[DG_MAXN];
+    T sinn[DG_MAXN];
+    T ce_s, ce_n;
+    T Ci[DG_MAXN][DG_MAXN];
+    T Q[DG_MAXN][DG_MAXN];
+    T rho[DG_MAXN];
+};
+
+// Host-side FP64 tables of one mesh.
+struct HostTables {
+    int n = 0, nm = 0, nlon = 0, nlat = 0;
+    double dlam = 0, dth = 0, R = 0;
+    double xg[DG_MAXN], wg[DG_MAXN];
+    double xm[32], wm[32];
+    BasisTab<double> basis;
+    RowTab<double> *rows = nullptr;   // nlat entries
+    double *C = nullptr;              // nlat * n * n: C_j itself (mass and projection)
+};
+
+// dg_tables.cpp
+void dg_gauss_legendre(int n, double *x, double *w);
+double dg_legendre(int k, double x);
+double dg_legendre_deriv(int k, double x);
+int dg_build_tables(HostTables &t, int nlon, int nlat, int p, double R, double g);
+void dg_free_tables(HostTables &t);
+
+// Stage-kernel launch description (dg_stage.cu).  One fused kernel computes
+// k = M^{-1} h(u_in) and writes
+//   out  = ca * P  + cb * u_in + cc * dt * k        (P may be null when ca == 0)
+//   out2 = ca2 * P2 + cc2 * dt * k                  (optional second output)
+template <typename T>
+struct StageArgs {
+    const T *u_in;
+    const T *P;
+    T *out;
+    const T *P2;
+    T *out2;
+    const RowTab<T> *rows;
+    unsigned int *status;
+    int nlon, nlat;
+    T href;          // reference depth: h = href + stored h
+    T P0;            // g href^2 / 2 (pressure carried by the rho table)
+    T g, cF, cG, invR, twoOmega;
+    T ca, cb, cc, ca2, cc2, dt;
+};
+
+// status bits written by device code
+#define DG_STATUS_NONPHYSICAL 1u
+#define DG_STATUS_NONFINITE 2u
+
+template <typename T>
+int dg_launch_stage(int n, const StageArgs<T> &a, void *stream);
+template <typename T>
+int dg_upload_basis(const BasisTab<double> *all);   // all[n-1] for n = 1..DG_MAXN
+
+// dg_aux.cu
+template <typename T>
+int dg_launch_to_internal(const double *src, T *dst, size_t nel, int nphi, double href, void *stream);
+template <typename T>
+int dg_launch_to_api(const T *src, double *dst, size_t nel, int nphi, double href, void *stream);
+template <typename T>
+int dg_launch_mass(const T *u, const double *c0, int nlon, int nlat, int n, double href, double dlam,
+                   double dth, double scale, double *partials, int nblocks, double *result, void *stream);
+template <typename T>
+int dg_launch_max_speed(const T *u, int nlon, int nlat, int n, double href, double g,
+                        unsigned long long *maxbits, unsigned int *status, void *stream);
+int dg_mass_blocks(size_t nel);

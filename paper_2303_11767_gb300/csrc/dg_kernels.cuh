@@ -1,0 +1,758 @@
+// dg_kernels.cuh -- device code of libdgswe, included once per precision by
+// dg_kernels_f32.cu / dg_kernels_f64.cu with DG_REAL defined to the element
+// type.  Each translation unit owns its constant basis tables.
+//
+// The fused stage kernel evaluates, for every element, the tendency
+//   k = M^{-1} h(u)   (paper Eq. ode)
+// of the weak form Eq. (dg_parts) for the shallow water system of Eq. (sph3):
+//   S1  modal -> Gauss-point values, sum-factorised (a-pass, then b-pass)
+//   S2  pointwise fluxes F, G and sources S with cos/sin(theta) row tables
+//   S3  volume integral, sum-factorised (beta-pass, then alpha-pass)
+//   S4  edge traces of the element; the tile's halo ring computes the traces
+//       its neighbours need, so no second pass over memory is made
+//   S5  Rusanov flux (Eq. rusanov) at every edge point, zero at pole edges
+//   S6  lift of the edge fluxes
+//   S7  inverse of the per-row cos(theta)-weighted mass matrix
+//   S8  Runge-Kutta combination and store
+// and all of it happens in one kernel launch per stage.
+//
+// Thread mapping: one warp owns G = 32 / N consecutive elements of one
+// latitude row; N lanes per element.  Lane k first owns row b = k of the modal
+// coefficients, then column alpha = k of the Gauss points (after a transpose
+// through shared memory), then row b = k again for the output.  A block of
+// DG_WARPS warps covers G x DG_WARPS elements.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+
+#include "dg_internal.h"
+
+#ifndef DG_REAL
+#error "define DG_REAL before including dg_kernels.cuh"
+#endif
+
+__constant__ BasisTab<DG_REAL> c_basis[DG_MAXN];
+
+namespace dgk {
+
+template <int N>
+struct Geo {
+    static constexpr int G = 32 / N;            // elements per warp
+    static constexpr int NP = N * N;            // modes per field
+    static constexpr int EL = 3 * NP;           // values per element
+    static constexpr int SA = N + 1;            // padded stride of transposed rows
+    static constexpr int T1_OFF = 0;            // [f][alpha][SA]
+    static constexpr int EW_OFF = 3 * N * SA;   // [f][2][N]
+    static constexpr int X_OFF = 0;             // [f][2][alpha][SA]   (reuses T1/EW)
+    static constexpr int FS_OFF = 6 * N * SA;   // [f][2][N]
+    static constexpr int WB_MIN = 6 * N * SA + 6 * N;
+    // element stride in the warp buffer, padded to spread groups over banks
+    static constexpr int WB = WB_MIN + ((N - (WB_MIN % 32)) % 32 + 32) % 32;
+    static constexpr int TW = G + 2;            // padded tile width (halo columns)
+    static constexpr int TH = DG_WARPS + 2;     // padded tile height (halo rows)
+    static constexpr int TRC = 4 * 3 * N;       // trace values per slot
+    static constexpr int HALO_MAX = 2 * DG_WARPS * N + 2 * G * N;
+    static_assert(HALO_MAX <= 32 * DG_WARPS, "halo items exceed the block");
+};
+
+template <typename T>
+__device__ __forceinline__ T rcp(T x) { return T(1) / x; }
+
+// Physical lambda-flux (hu, hu u + P, hu v) of a state q = (h', hu, hv) with
+// h = href + h' and the pressure P = g h' (href + h'/2) (the constant part
+// g href^2/2 is carried by the rho table), and the wave speed |u| + sqrt(g h).
+template <typename T>
+__device__ __forceinline__ void lam_flux(const T *q, T href, T g, T *f, T &speed, unsigned &st)
+{
+    const T h = href + q[0];
+    if (!(h > T(0))) st |= DG_STATUS_NONPHYSICAL;
+    const T u = q[1] * rcp(h);
+    const T P = q[0] * g * (href + T(0.5) * q[0]);
+    f[0] = q[1];
+    f[1] = q[1] * u + P;
+    f[2] = q[2] * u;
+    speed = fabs(u) + sqrt(g * h);
+}
+
+template <typename T>
+__device__ __forceinline__ void th_flux(const T *q, T href, T g, T *f, T &speed, unsigned &st)
+{
+    const T h = href + q[0];
+    if (!(h > T(0))) st |= DG_STATUS_NONPHYSICAL;
+    const T v = q[2] * rcp(h);
+    const T P = q[0] * g * (href + T(0.5) * q[0]);
+    f[0] = q[2];
+    f[1] = q[1] * v;
+    f[2] = q[2] * v + P;
+    speed = fabs(v) + sqrt(g * h);
+}
+
+// Rusanov flux through a lambda-face, left state L (west), right state R
+// (east): F* = (F(L) + F(R))/2 - alpha/2 (R - L) with alpha the larger
+// one-sided |u| + c; the cos(theta) of U = cos(theta) q cancels against the
+// 1/cos(theta) of the eigenvalue of dF/dU.  Scaled by cF = 2/(R dlambda).
+template <typename T>
+__device__ __forceinline__ void rusanov_lam(const T *L, const T *R, T href, T g, T cF, T *out, unsigned &st)
+{
+    T fl[3], fr[3], al, ar;
+    lam_flux(L, href, g, fl, al, st);
+    lam_flux(R, href, g, fr, ar, st);
+    const T a = fmax(al, ar);
+#pragma unroll
+    for (int f = 0; f < 3; ++f) out[f] = cF * (T(0.5) * (fl[f] + fr[f]) - T(0.5) * a * (R[f] - L[f]));
+}
+
+// Rusanov flux through a theta-face, lower state S, upper state N, times the
+// edge cos(theta) ce (flux and jump of U both carry it); scaled by cG.
+template <typename T>
+__device__ __forceinline__ void rusanov_th(const T *S, const T *Nq, T href, T g, T cGce, T *out, unsigned &st)
+{
+    T fs[3], fn[3], as, an;
+    th_flux(S, href, g, fs, as, st);
+    th_flux(Nq, href, g, fn, an, st);
+    const T a = fmax(as, an);
+#pragma unroll
+    for (int f = 0; f < 3; ++f) out[f] = cGce * (T(0.5) * (fs[f] + fn[f]) - T(0.5) * a * (Nq[f] - S[f]));
+}
+
+template <typename T, int N>
+__device__ __forceinline__ void load_row(const T *__restrict__ p, T *o)
+{
+#pragma unroll
+    for (int a = 0; a < N; ++a) o[a] = __ldg(p + a);
+}
+
+template <>
+__device__ __forceinline__ void load_row<float, 4>(const float *__restrict__ p, float *o)
+{
+    const float4 v = __ldg(reinterpret_cast<const float4 *>(p));
+    o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+}
+
+template <>
+__device__ __forceinline__ void load_row<float, 2>(const float *__restrict__ p, float *o)
+{
+    const float2 v = __ldg(reinterpret_cast<const float2 *>(p));
+    o[0] = v.x; o[1] = v.y;
+}
+
+template <>
+__device__ __forceinline__ void load_row<double, 2>(const double *__restrict__ p, double *o)
+{
+    const double2 v = __ldg(reinterpret_cast<const double2 *>(p));
+    o[0] = v.x; o[1] = v.y;
+}
+
+template <>
+__device__ __forceinline__ void load_row<double, 4>(const double *__restrict__ p, double *o)
+{
+    const double2 v0 = __ldg(reinterpret_cast<const double2 *>(p));
+    const double2 v1 = __ldg(reinterpret_cast<const double2 *>(p) + 1);
+    o[0] = v0.x; o[1] = v0.y; o[2] = v1.x; o[3] = v1.y;
+}
+
+template <typename T, int N>
+__device__ __forceinline__ void store_row(T *p, const T *o)
+{
+#pragma unroll
+    for (int a = 0; a < N; ++a) p[a] = o[a];
+}
+
+template <>
+__device__ __forceinline__ void store_row<float, 4>(float *p, const float *o)
+{
+    *reinterpret_cast<float4 *>(p) = make_float4(o[0], o[1], o[2], o[3]);
+}
+
+template <>
+__device__ __forceinline__ void store_row<float, 2>(float *p, const float *o)
+{
+    *reinterpret_cast<float2 *>(p) = make_float2(o[0], o[1]);
+}
+
+template <>
+__device__ __forceinline__ void store_row<double, 2>(double *p, const double *o)
+{
+    *reinterpret_cast<double2 *>(p) = make_double2(o[0], o[1]);
+}
+
+template <>
+__device__ __forceinline__ void store_row<double, 4>(double *p, const double *o)
+{
+    reinterpret_cast<double2 *>(p)[0] = make_double2(o[0], o[1]);
+    reinterpret_cast<double2 *>(p)[1] = make_double2(o[2], o[3]);
+}
+
+template <typename T, int N>
+__global__ void __launch_bounds__(32 * DG_WARPS) stage_kernel(const StageArgs<T> A)
+{
+    using GE = Geo<N>;
+    constexpr int G = GE::G, NP = GE::NP, EL = GE::EL, SA = GE::SA, WB = GE::WB;
+    constexpr int TW = GE::TW, TRC = GE::TRC;
+    const BasisTab<T> &B = c_basis[N - 1];
+
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *wbuf = reinterpret_cast<T *>(smem_raw);
+    T *trc = wbuf + DG_WARPS * G * WB;
+
+    const int tid = threadIdx.x;
+    const int warp = tid >> 5, lane = tid & 31;
+    const int g = lane / N, k = lane - (lane / N) * N;
+    const bool lane_ok = g < G;
+    const int i0 = blockIdx.x * G, j0 = blockIdx.y * DG_WARPS;
+    const int Gv = min(G, A.nlon - i0);
+    const int Wv = min(DG_WARPS, A.nlat - j0);
+    const int i = i0 + g, j = j0 + warp;
+    const bool valid = lane_ok && g < Gv && warp < Wv;
+    const size_t e = valid ? (size_t)j * A.nlon + i : 0;
+    const T href = A.href, gg = A.g;
+    unsigned st = 0;
+
+    T *wb = wbuf + (warp * G + (lane_ok ? g : 0)) * WB;
+
+    // ---- S0: own modal row b = k of the three fields
+    T uh[3][N];
+#pragma unroll
+    for (int f = 0; f < 3; ++f) {
+        if (valid) load_row<T, N>(A.u_in + e * EL + f * NP + k * N, uh[f]);
+        else {
+#pragma unroll
+            for (int a = 0; a < N; ++a) uh[f][a] = T(0);
+        }
+    }
+
+    // ---- S1 a-pass (row b = k): t1[alpha] = sum_a L_a(xi_alpha) u[b][a], and
+    //      the lambda-edge partial sums sum_a L_a(+-1) u[b][a]
+    if (lane_ok) {
+#pragma unroll
+        for (int f = 0; f < 3; ++f) {
+#pragma unroll
+            for (int q = 0; q < N; ++q) {
+                T s = T(0);
+#pragma unroll
+                for (int a = 0; a < N; ++a) s = fma(B.LV[a][q], uh[f][a], s);
+                wb[GE::T1_OFF + (f * N + q) * SA + k] = s;
+            }
+            T se = T(0), sw = T(0);
+#pragma unroll
+            for (int a = 0; a < N; ++a) {
+                se = fma(B.SE[a], uh[f][a], se);
+                sw = fma(B.SW[a], uh[f][a], sw);
+            }
+            wb[GE::EW_OFF + (f * 2 + 0) * N + k] = se;
+            wb[GE::EW_OFF + (f * 2 + 1) * N + k] = sw;
+        }
+    }
+    __syncwarp();
+
+    // ---- S1 b-pass (column alpha = k) and S4 own traces
+    T qn[3][N];      // Gauss-point values at (alpha = k, beta)
+    T tr[4][3];      // traces at own point k: W, E (at eta_k), S, N (at xi_k)
+    {
+        T LVk[N];
+#pragma unroll
+        for (int b = 0; b < N; ++b) LVk[b] = B.LV[b][k];
+#pragma unroll
+        for (int f = 0; f < 3; ++f) {
+            T c[N], ee[N], ew[N];
+#pragma unroll
+            for (int b = 0; b < N; ++b) {
+                c[b] = wb[GE::T1_OFF + (f * N + k) * SA + b];
+                ee[b] = wb[GE::EW_OFF + (f * 2 + 0) * N + b];
+                ew[b] = wb[GE::EW_OFF + (f * 2 + 1) * N + b];
+            }
+#pragma unroll
+            for (int q = 0; q < N; ++q) {
+                T s = T(0);
+#pragma unroll
+                for (int b = 0; b < N; ++b) s = fma(B.LV[b][q], c[b], s);
+                qn[f][q] = s;
+            }
+            T ts = T(0), tn = T(0), tw = T(0), te = T(0);
+#pragma unroll
+            for (int b = 0; b < N; ++b) {
+                ts = fma(B.SW[b], c[b], ts);
+                tn = fma(B.SE[b], c[b], tn);
+                tw = fma(LVk[b], ew[b], tw);
+                te = fma(LVk[b], ee[b], te);
+            }
+            tr[0][f] = tw; tr[1][f] = te; tr[2][f] = ts; tr[3][f] = tn;
+        }
+    }
+    if (valid) {
+        T *slot = trc + ((warp + 1) * TW + (g + 1)) * TRC;
+#pragma unroll
+        for (int s = 0; s < 4; ++s)
+#pragma unroll
+            for (int f = 0; f < 3; ++f) slot[(s * 3 + f) * N + k] = tr[s][f];
+    }
+
+    // ---- S4 halo: traces of the ring of neighbour elements facing the tile
+    {
+        const int nWE = Wv * N;
+        const bool hasS = j0 > 0, hasN = j0 + Wv < A.nlat;
+        const int nS = hasS ? Gv * N : 0, nN = hasN ? Gv * N : 0;
+        int it = tid;
+        if (it < 2 * nWE + nS + nN) {
+            int he_i, he_j, side, kk, sl;
+            if (it < 2 * nWE) {                 // west / east halo columns
+                const bool east = it >= nWE;
+                const int r = east ? it - nWE : it;
+                const int w = r / N;
+                kk = r - w * N;
+                he_j = j0 + w;
+                he_i = east ? (i0 + Gv) % A.nlon : (i0 - 1 + A.nlon) % A.nlon;
+                side = east ? 0 : 1;            // east halo needs its W trace
+                sl = (w + 1) * TW + (east ? Gv + 1 : 0);
+            } else {                            // south / north halo rows
+                const int r0 = it - 2 * nWE;
+                const bool north = r0 >= nS;
+                const int r = north ? r0 - nS : r0;
+                const int c = r / N;
+                kk = r - c * N;
+                he_i = i0 + c;
+                he_j = north ? j0 + Wv : j0 - 1;
+                side = north ? 2 : 3;           // north halo needs its S trace
+                sl = (north ? Wv + 1 : 0) * TW + c + 1;
+            }
+            const T *src = A.u_in + ((size_t)he_j * A.nlon + he_i) * EL;
+            T *slot = trc + sl * TRC;
+#pragma unroll
+            for (int f = 0; f < 3; ++f) {
+                T acc = T(0);
+                if (side <= 1) {                // lambda edge: sum_b L_b(eta_kk) sum_a L_a(+-1) u[b][a]
+#pragma unroll
+                    for (int b = 0; b < N; ++b) {
+                        T row[N];
+                        load_row<T, N>(src + f * NP + b * N, row);
+                        T s = T(0);
+#pragma unroll
+                        for (int a = 0; a < N; ++a) s = fma(side == 1 ? B.SE[a] : B.SW[a], row[a], s);
+                        acc = fma(B.LV[b][kk], s, acc);
+                    }
+                } else {                        // theta edge: sum_b L_b(+-1) sum_a L_a(xi_kk) u[b][a]
+#pragma unroll
+                    for (int b = 0; b < N; ++b) {
+                        T row[N];
+                        load_row<T, N>(src + f * NP + b * N, row);
+                        T s = T(0);
+#pragma unroll
+                        for (int a = 0; a < N; ++a) s = fma(B.LV[a][kk], row[a], s);
+                        acc = fma(side == 3 ? B.SE[b] : B.SW[b], s, acc);
+                    }
+                }
+                slot[(side * 3 + f) * N + kk] = acc;
+            }
+        }
+    }
+    __syncthreads();
+
+    // ---- S5 Rusanov fluxes at own edge points (W, E at eta_k; S, N at xi_k)
+    const RowTab<T> *RT = A.rows + (valid ? j : 0);
+    T FsW[3], FsE[3], GsS[3], GsN[3];
+    {
+        const T *own = trc + ((warp + 1) * TW + (g + 1)) * TRC;
+        const T *sW = own - TRC, *sE = own + TRC;
+        const T *sS = own - TW * TRC, *sN = own + TW * TRC;
+        T nb[3];
+#pragma unroll
+        for (int f = 0; f < 3; ++f) nb[f] = valid ? sW[(1 * 3 + f) * N + k] : tr[0][f];
+        rusanov_lam(nb, tr[0], href, gg, A.cF, FsW, st);
+#pragma unroll
+        for (int f = 0; f < 3; ++f) nb[f] = valid ? sE[(0 * 3 + f) * N + k] : tr[1][f];
+        rusanov_lam(tr[1], nb, href, gg, A.cF, FsE, st);
+        const T ces = __ldg(&RT->ce_s), cen = __ldg(&RT->ce_n);
+        if (valid && j > 0) {
+#pragma unroll
+            for (int f = 0; f < 3; ++f) nb[f] = sS[(3 * 3 + f) * N + k];
+            rusanov_th(nb, tr[2], href, gg, A.cG * ces, GsS, st);
+        } else {
+#pragma unroll
+            for (int f = 0; f < 3; ++f) GsS[f] = T(0);   // pole edge: zero flux
+        }
+        if (valid && j < A.nlat - 1) {
+#pragma unroll
+            for (int f = 0; f < 3; ++f) nb[f] = sN[(2 * 3 + f) * N + k];
+            rusanov_th(tr[3], nb, href, gg, A.cG * cen, GsN, st);
+        } else {
+#pragma unroll
+            for (int f = 0; f < 3; ++f) GsN[f] = T(0);   // pole edge: zero flux
+        }
+    }
+
+    // ---- S2 pointwise fluxes at (alpha = k, beta) and S3 beta-pass, with the
+    //      N/S lift folded in and the inverse mass matrix applied along b
+    {
+        T X1[3][N], X2[3][N];
+#pragma unroll
+        for (int f = 0; f < 3; ++f)
+#pragma unroll
+            for (int b = 0; b < N; ++b) { X1[f][b] = T(0); X2[f][b] = T(0); }
+#pragma unroll
+        for (int q = 0; q < N; ++q) {
+            const T hp = qn[0][q], hu = qn[1][q], hv = qn[2][q];
+            const T h = href + hp;
+            if (!(h > T(0))) st |= DG_STATUS_NONPHYSICAL;
+            const T rh = rcp(h);
+            const T u = hu * rh, v = hv * rh;
+            const T P = hp * gg * (href + T(0.5) * hp);
+            const T c = __ldg(&RT->cosn[q]), s = __ldg(&RT->sinn[q]);
+            const T F0 = A.cF * hu, F1 = A.cF * fma(hu, u, P), F2 = A.cF * (hu * v);
+            const T cGc = A.cG * c;
+            const T G0 = cGc * hv, G1 = cGc * (hv * u), G2 = cGc * fma(hv, v, P);
+            const T K = s * fma(A.twoOmega, c, u * A.invR);
+            const T S1 = K * hv, S2 = -(P * s * A.invR) - K * hu;
+#pragma unroll
+            for (int b = 0; b < N; ++b) {
+                const T wl = B.WLV[b][q], wd = B.WLD[b][q];
+                X1[0][b] = fma(wl, F0, X1[0][b]);
+                X1[1][b] = fma(wl, F1, X1[1][b]);
+                X1[2][b] = fma(wl, F2, X1[2][b]);
+                X2[0][b] = fma(wd, G0, X2[0][b]);
+                X2[1][b] = fma(wd, G1, fma(wl, S1, X2[1][b]));
+                X2[2][b] = fma(wd, G2, fma(wl, S2, X2[2][b]));
+            }
+        }
+#pragma unroll
+        for (int f = 0; f < 3; ++f)
+#pragma unroll
+            for (int b = 0; b < N; ++b) X2[f][b] -= B.SE[b] * GsN[f] - B.SW[b] * GsS[f];
+        // S7 inverse mass matrix along b (per row table), then hand over
+        if (lane_ok) {
+#pragma unroll
+            for (int f = 0; f < 3; ++f)
+#pragma unroll
+                for (int b = 0; b < N; ++b) {
+                    T y1 = T(0), y2 = T(0);
+#pragma unroll
+                    for (int c = 0; c < N; ++c) {
+                        const T ci = __ldg(&RT->Ci[b][c]);
+                        y1 = fma(ci, X1[f][c], y1);
+                        y2 = fma(ci, X2[f][c], y2);
+                    }
+                    wb[GE::X_OFF + ((f * 2 + 0) * N + k) * SA + b] = y1;
+                    wb[GE::X_OFF + ((f * 2 + 1) * N + k) * SA + b] = y2;
+                }
+#pragma unroll
+            for (int f = 0; f < 3; ++f) {
+                wb[GE::FS_OFF + (f * 2 + 0) * N + k] = FsE[f];
+                wb[GE::FS_OFF + (f * 2 + 1) * N + k] = FsW[f];
+            }
+        }
+    }
+    __syncwarp();
+
+    // ---- S3 alpha-pass and S6 E/W lift (row b = k), S8 combine and store
+    {
+        T Qk[N];
+#pragma unroll
+        for (int q = 0; q < N; ++q) Qk[q] = __ldg(&RT->Q[k][q]);
+        const T rhok = __ldg(&RT->rho[k]);
+        T kk[3][N];
+#pragma unroll
+        for (int f = 0; f < 3; ++f) {
+            T y1[N], y2[N];
+            T ye = T(0), yw = T(0);
+#pragma unroll
+            for (int q = 0; q < N; ++q) {
+                y1[q] = wb[GE::X_OFF + ((f * 2 + 0) * N + q) * SA + k];
+                y2[q] = wb[GE::X_OFF + ((f * 2 + 1) * N + q) * SA + k];
+                ye = fma(Qk[q], wb[GE::FS_OFF + (f * 2 + 0) * N + q], ye);
+                yw = fma(Qk[q], wb[GE::FS_OFF + (f * 2 + 1) * N + q], yw);
+            }
+#pragma unroll
+            for (int a = 0; a < N; ++a) {
+                T s = T(0);
+#pragma unroll
+                for (int q = 0; q < N; ++q) s = fma(B.WLD[a][q], y1[q], fma(B.WLV[a][q], y2[q], s));
+                kk[f][a] = s - (B.SE[a] * ye - B.SW[a] * yw);
+            }
+        }
+        kk[2][0] = fma(A.P0, rhok, kk[2][0]);
+
+        if (valid) {
+            const T cdt = A.cc * A.dt;
+#pragma unroll
+            for (int f = 0; f < 3; ++f) {
+                T o[N], pr[N];
+                if (A.ca != T(0)) load_row<T, N>(A.P + e * EL + f * NP + k * N, pr);
+                else {
+#pragma unroll
+                    for (int a = 0; a < N; ++a) pr[a] = T(0);
+                }
+#pragma unroll
+                for (int a = 0; a < N; ++a) {
+                    o[a] = fma(cdt, kk[f][a], fma(A.cb, uh[f][a], A.ca * pr[a]));
+                    if (!isfinite(o[a])) st |= DG_STATUS_NONFINITE;
+                }
+                store_row<T, N>(A.out + e * EL + f * NP + k * N, o);
+            }
+            if (A.out2) {
+                const T cdt2 = A.cc2 * A.dt;
+#pragma unroll
+                for (int f = 0; f < 3; ++f) {
+                    T o[N], pr[N];
+                    load_row<T, N>(A.P2 + e * EL + f * NP + k * N, pr);
+#pragma unroll
+                    for (int a = 0; a < N; ++a) o[a] = fma(cdt2, kk[f][a], A.ca2 * pr[a]);
+                    store_row<T, N>(A.out2 + e * EL + f * NP + k * N, o);
+                }
+            }
+        }
+    }
+    if (st && valid) atomicOr(A.status, st);
+}
+
+template <typename T, int N>
+size_t stage_smem_bytes()
+{
+    using GE = Geo<N>;
+    return sizeof(T) * ((size_t)DG_WARPS * GE::G * GE::WB + (size_t)GE::TW * GE::TH * GE::TRC);
+}
+
+template <typename T, int N>
+int launch_stage_n(const StageArgs<T> &a, cudaStream_t s)
+{
+    using GE = Geo<N>;
+    const size_t smem = stage_smem_bytes<T, N>();
+    // the shared-memory opt-in is a per-device function attribute
+    static unsigned long long attr_set = 0;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 1;
+    if (!(attr_set >> dev & 1ull)) {
+        if (cudaFuncSetAttribute(stage_kernel<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+            cudaSuccess)
+            return 1;
+        attr_set |= 1ull << dev;
+    }
+    dim3 grid((a.nlon + GE::G - 1) / GE::G, (a.nlat + DG_WARPS - 1) / DG_WARPS);
+    stage_kernel<T, N><<<grid, 32 * DG_WARPS, smem, s>>>(a);
+    return cudaPeekAtLastError() == cudaSuccess ? 0 : 1;
+}
+
+// ------------------------------------------------------------- auxiliary --
+
+// API layout (FP64, full h) <-> internal layout (T, h stored relative to href).
+template <typename T>
+__global__ void to_internal_kernel(const double *__restrict__ src, T *__restrict__ dst, size_t nval, int per_el,
+                                   int nphi, double href)
+{
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < nval; t += (size_t)gridDim.x * blockDim.x) {
+        double v = src[t];
+        if (t % per_el == 0) v -= 2.0 * href;   // mode 0 of h: phi_0 = 1/2
+        dst[t] = (T)v;
+    }
+    (void)nphi;
+}
+
+template <typename T>
+__global__ void to_api_kernel(const T *__restrict__ src, double *__restrict__ dst, size_t nval, int per_el,
+                              double href)
+{
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < nval; t += (size_t)gridDim.x * blockDim.x) {
+        double v = (double)src[t];
+        if (t % per_el == 0) v += 2.0 * href;
+        dst[t] = v;
+    }
+}
+
+// Neumaier-compensated pair (sum, correction); combining two pairs uses the
+// error-free TwoSum of the sums, so the fixed reduction tree below gives the
+// same bits on every run.
+struct CSum {
+    double s, c;
+};
+
+__device__ __forceinline__ CSum csum_add(CSum a, double x)
+{
+    const double t = a.s + x;
+    const double bp = t - a.s;
+    const double err = (a.s - (t - bp)) + (x - bp);
+    return CSum{t, a.c + err};
+}
+
+__device__ __forceinline__ CSum csum_merge(CSum a, CSum b)
+{
+    CSum r = csum_add(a, b.s);
+    r.c += b.c;
+    return r;
+}
+
+constexpr int MASS_THREADS = 256;
+
+// Per element: int h cos(theta) dlambda dtheta
+//   = (dlam dth / 2) sum_b C_j[0][b] h'_{a=0,b} + href dlam (sin t - sin b).
+// c0: nlat * n values C_j[0][b]; area row j in c0[nlat*n + j].
+template <typename T>
+__global__ void __launch_bounds__(MASS_THREADS) mass_partial_kernel(const T *__restrict__ u,
+                                                                    const double *__restrict__ c0, int nlon,
+                                                                    int nlat, int n, double href, double half_dd,
+                                                                    double dlam, size_t chunk,
+                                                                    double *__restrict__ partials)
+{
+    __shared__ CSum red[MASS_THREADS];
+    const size_t nel = (size_t)nlon * nlat;
+    const size_t b0 = blockIdx.x * chunk, b1 = min(nel, b0 + chunk);
+    const int per = 3 * n * n;
+    CSum acc{0.0, 0.0};
+    for (size_t e = b0 + threadIdx.x; e < b1; e += MASS_THREADS) {
+        const int j = (int)(e / nlon);
+        const T *ue = u + e * per;
+        double m = 0.0;
+        for (int b = 0; b < n; ++b) m += c0[j * n + b] * (double)ue[b * n];
+        acc = csum_add(acc, half_dd * m + href * dlam * c0[nlat * n + j]);
+    }
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int s = MASS_THREADS / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) red[threadIdx.x] = csum_merge(red[threadIdx.x], red[threadIdx.x + s]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        partials[2 * blockIdx.x] = red[0].s;
+        partials[2 * blockIdx.x + 1] = red[0].c;
+    }
+}
+
+static __global__ void __launch_bounds__(MASS_THREADS) mass_final_kernel(const double *__restrict__ partials, int nblocks,
+                                                                  double scale, double *__restrict__ result)
+{
+    __shared__ CSum red[MASS_THREADS];
+    CSum acc{0.0, 0.0};
+    for (int b = threadIdx.x; b < nblocks; b += MASS_THREADS)
+        acc = csum_merge(acc, CSum{partials[2 * b], partials[2 * b + 1]});
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int s = MASS_THREADS / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) red[threadIdx.x] = csum_merge(red[threadIdx.x], red[threadIdx.x + s]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *result = scale * (red[0].s + red[0].c);
+}
+
+// Largest sqrt(u^2 + v^2) + sqrt(g h) over the n x n Gauss points; one thread
+// per element.  Positive doubles order like their bit patterns, so an atomic
+// max on the bits is exact and order independent.
+template <typename T, int N>
+__global__ void max_speed_kernel(const T *__restrict__ u, int nel, double href, double g,
+                                 unsigned long long *maxbits, unsigned *status)
+{
+    const BasisTab<T> &B = c_basis[N - 1];
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    double best = 0.0;
+    unsigned st = 0;
+    if (e < nel) {
+        const T *ue = u + (size_t)e * 3 * N * N;
+        for (int q = 0; q < N; ++q)
+            for (int r = 0; r < N; ++r) {
+                double qv[3];
+                for (int f = 0; f < 3; ++f) {
+                    double s = 0.0;
+                    for (int b = 0; b < N; ++b) {
+                        double t = 0.0;
+                        for (int a = 0; a < N; ++a) t += (double)B.LV[a][r] * (double)ue[f * N * N + b * N + a];
+                        s += (double)B.LV[b][q] * t;
+                    }
+                    qv[f] = s;
+                }
+                const double h = href + qv[0];
+                if (!(h > 0.0)) { st |= DG_STATUS_NONPHYSICAL; continue; }
+                const double uu = qv[1] / h, vv = qv[2] / h;
+                best = fmax(best, sqrt(uu * uu + vv * vv) + sqrt(g * h));
+            }
+    }
+    for (int o = 16; o > 0; o >>= 1) best = fmax(best, __shfl_xor_sync(0xffffffffu, best, o));
+    if ((threadIdx.x & 31) == 0 && best > 0.0) atomicMax(maxbits, (unsigned long long)__double_as_longlong(best));
+    if (st) atomicOr(status, st);
+}
+
+}  // namespace dgk
+
+// ------------------------------------------------------ host-side launchers --
+
+template <>
+int dg_upload_basis<DG_REAL>(const BasisTab<double> *all)
+{
+    BasisTab<DG_REAL> t[DG_MAXN];
+    for (int n = 0; n < DG_MAXN; ++n) {
+        for (int a = 0; a < DG_MAXN; ++a) {
+            t[n].SE[a] = (DG_REAL)all[n].SE[a];
+            t[n].SW[a] = (DG_REAL)all[n].SW[a];
+            for (int q = 0; q < DG_MAXN; ++q) {
+                t[n].LV[a][q] = (DG_REAL)all[n].LV[a][q];
+                t[n].WLV[a][q] = (DG_REAL)all[n].WLV[a][q];
+                t[n].WLD[a][q] = (DG_REAL)all[n].WLD[a][q];
+            }
+        }
+    }
+    return cudaMemcpyToSymbol(c_basis, t, sizeof(t)) == cudaSuccess ? 0 : 1;
+}
+
+template <>
+int dg_launch_stage<DG_REAL>(int n, const StageArgs<DG_REAL> &a, void *stream)
+{
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    switch (n) {
+    case 1: return dgk::launch_stage_n<DG_REAL, 1>(a, s);
+    case 2: return dgk::launch_stage_n<DG_REAL, 2>(a, s);
+    case 3: return dgk::launch_stage_n<DG_REAL, 3>(a, s);
+    case 4: return dgk::launch_stage_n<DG_REAL, 4>(a, s);
+    case 5: return dgk::launch_stage_n<DG_REAL, 5>(a, s);
+    default: return 1;
+    }
+}
+
+template <>
+int dg_launch_to_internal<DG_REAL>(const double *src, DG_REAL *dst, size_t nel, int nphi, double href, void *stream)
+{
+    const size_t nval = nel * 3 * nphi;
+    const int threads = 256;
+    const size_t blocks = (nval + threads - 1) / threads;
+    dgk::to_internal_kernel<DG_REAL><<<(unsigned)(blocks < 65535 * 16 ? blocks : 65535 * 16), threads, 0,
+                                       static_cast<cudaStream_t>(stream)>>>(src, dst, nval, 3 * nphi, nphi, href);
+    return cudaPeekAtLastError() == cudaSuccess ? 0 : 1;
+}
+
+template <>
+int dg_launch_to_api<DG_REAL>(const DG_REAL *src, double *dst, size_t nel, int nphi, double href, void *stream)
+{
+    const size_t nval = nel * 3 * nphi;
+    const int threads = 256;
+    const size_t blocks = (nval + threads - 1) / threads;
+    dgk::to_api_kernel<DG_REAL><<<(unsigned)(blocks < 65535 * 16 ? blocks : 65535 * 16), threads, 0,
+                                  static_cast<cudaStream_t>(stream)>>>(src, dst, nval, 3 * nphi, href);
+    return cudaPeekAtLastError() == cudaSuccess ? 0 : 1;
+}
+
+template <>
+int dg_launch_mass<DG_REAL>(const DG_REAL *u, const double *c0, int nlon, int nlat, int n, double href, double dlam,
+                            double dth, double scale, double *partials, int nblocks, double *result, void *stream)
+{
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const size_t nel = (size_t)nlon * nlat;
+    const size_t chunk = (nel + nblocks - 1) / nblocks;
+    dgk::mass_partial_kernel<DG_REAL><<<nblocks, dgk::MASS_THREADS, 0, s>>>(u, c0, nlon, nlat, n, href,
+                                                                            0.5 * dlam * dth, dlam, chunk, partials);
+    dgk::mass_final_kernel<<<1, dgk::MASS_THREADS, 0, s>>>(partials, nblocks, scale, result);
+    return cudaPeekAtLastError() == cudaSuccess ? 0 : 1;
+}
+
+template <>
+int dg_launch_max_speed<DG_REAL>(const DG_REAL *u, int nlon, int nlat, int n, double href, double g,
+                                 unsigned long long *maxbits, unsigned int *status, void *stream)
+{
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int nel = nlon * nlat;
+    const int threads = 128;
+    const int blocks = (nel + threads - 1) / threads;
+    switch (n) {
+    case 1: dgk::max_speed_kernel<DG_REAL, 1><<<blocks, threads, 0, s>>>(u, nel, href, g, maxbits, status); break;
+    case 2: dgk::max_speed_kernel<DG_REAL, 2><<<blocks, threads, 0, s>>>(u, nel, href, g, maxbits, status); break;
+    case 3: dgk::max_speed_kernel<DG_REAL, 3><<<blocks, threads, 0, s>>>(u, nel, href, g, maxbits, status); break;
+    case 4: dgk::max_speed_kernel<DG_REAL, 4><<<blocks, threads, 0, s>>>(u, nel, href, g, maxbits, status); break;
+    case 5: dgk::max_speed_kernel<DG_REAL, 5><<<blocks, threads, 0, s>>>(u, nel, href, g, maxbits, status); break;
+    default: return 1;
+    }
+    return cudaPeekAtLastError() == cudaSuccess ? 0 : 1;
+}

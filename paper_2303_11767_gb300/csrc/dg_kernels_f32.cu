@@ -1,0 +1,4 @@
+// FP32 instantiation of the device code (tables applied in FP32, tables and
+// mass sums built and reduced in FP64).
+#define DG_REAL float
+#include "dg_kernels.cuh"

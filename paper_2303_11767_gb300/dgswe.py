@@ -1,0 +1,222 @@
+"""Python binding of libdgswe (include/dgswe.h): argument marshalling only.
+
+Every computation runs in the CUDA library.  Importing this module does not
+load the library; the first Solver (or an explicit ``lib()``) does, and it
+raises if ``libdgswe.so`` has not been built (``__graft_entry__.build()`` or
+``python paper_2303_11767_gb300/build.py``).  There is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libdgswe.so")
+
+DG_OK, DG_EINVAL, DG_ENOMEM, DG_ECUDA, DG_ENONFINITE, DG_ENONPHYSICAL, DG_ETIMEOUT, DG_EUNSUPPORTED = range(8)
+STATUS_NAMES = {0: "DG_OK", 1: "DG_EINVAL", 2: "DG_ENOMEM", 3: "DG_ECUDA", 4: "DG_ENONFINITE",
+                5: "DG_ENONPHYSICAL", 6: "DG_ETIMEOUT", 7: "DG_EUNSUPPORTED"}
+PREC = {"fp64": 0, "fp32": 1, "fp32_tc_bf16": 2, "fp32_tc_fp16": 3}
+OPT_PRECISION, OPT_RK_ORDER, OPT_CHECK_FINITE, OPT_ALPHA_MODE, OPT_STREAM, OPT_STEPS_PER_GRAPH = 1, 2, 3, 4, 5, 6
+
+EARTH_RADIUS = 6.37122e6
+GRAVITY = 9.80616
+OMEGA = 7.292e-5
+
+# every entry point of include/dgswe.h: name -> (restype, argtypes)
+_dp = ctypes.POINTER(ctypes.c_double)
+_H = ctypes.c_void_p
+SIGNATURES = {
+    "dg_set_device": (ctypes.c_int, [ctypes.c_int]),
+    "dg_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                 ctypes.c_double, ctypes.POINTER(ctypes.c_void_p)]),
+    "dg_destroy": (ctypes.c_int, [_H]),
+    "dg_set_option": (ctypes.c_int, [_H, ctypes.c_int, ctypes.c_longlong]),
+    "dg_state_len": (ctypes.c_size_t, [_H]),
+    "dg_set_state": (ctypes.c_int, [_H, _dp, ctypes.c_size_t]),
+    "dg_get_state": (ctypes.c_int, [_H, _dp, ctypes.c_size_t]),
+    "dg_set_state_device": (ctypes.c_int, [_H, ctypes.c_void_p, ctypes.c_size_t]),
+    "dg_get_state_device": (ctypes.c_int, [_H, ctypes.c_void_p, ctypes.c_size_t]),
+    "dg_rhs": (ctypes.c_int, [_H, _dp, _dp, ctypes.c_size_t]),
+    "dg_step": (ctypes.c_int, [_H, ctypes.c_int, ctypes.c_double]),
+    "dg_total_mass": (ctypes.c_int, [_H, _dp]),
+    "dg_total_mass_device": (ctypes.c_int, [_H, ctypes.c_void_p]),
+    "dg_max_dt": (ctypes.c_int, [_H, ctypes.c_double, _dp]),
+    "dg_projection_nodes": (ctypes.c_int, [_H, _dp, ctypes.c_size_t, _dp, ctypes.c_size_t]),
+    "dg_project_nodal": (ctypes.c_int, [_H, _dp, ctypes.c_size_t, _dp, ctypes.c_size_t]),
+    "dg_get_time": (ctypes.c_int, [_H, _dp]),
+    "dg_set_time": (ctypes.c_int, [_H, ctypes.c_double]),
+    "dg_stage_launches": (ctypes.c_longlong, [_H]),
+    "dg_last_error": (ctypes.c_char_p, [_H]),
+}
+
+_lib = None
+
+
+class DGError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+def lib(path: str = LIB_PATH):
+    """Load libdgswe.so; raises if it is missing (no fallback)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise ImportError(f"libdgswe.so not built at {path}; run __graft_entry__.build()")
+        L = ctypes.CDLL(path)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(_dp)
+
+
+def _check(status, h=None):
+    if status != DG_OK:
+        msg = lib().dg_last_error(h)
+        raise DGError(status, msg.decode() if msg else "")
+
+
+def set_device(device: int):
+    _check(lib().dg_set_device(int(device)))
+
+
+class Solver:
+    """One mesh, one resident state (see include/dgswe.h for the semantics)."""
+
+    def __init__(self, nlon, nlat, degree, radius=EARTH_RADIUS, g=GRAVITY, omega=OMEGA, precision="fp64",
+                 rk_order=3, check_finite=True):
+        L = lib()
+        h = ctypes.c_void_p()
+        _check(L.dg_create(int(nlon), int(nlat), int(degree), float(radius), float(g), float(omega),
+                           ctypes.byref(h)))
+        self._h = h
+        self.nlon, self.nlat, self.degree = int(nlon), int(nlat), int(degree)
+        self.n = self.degree + 1
+        self.nphi = self.n * self.n
+        self.nm = self.degree + 9
+        self.radius, self.g, self.omega = float(radius), float(g), float(omega)
+        self.set_option(OPT_PRECISION, PREC[precision] if isinstance(precision, str) else int(precision))
+        self.set_option(OPT_RK_ORDER, rk_order)
+        self.set_option(OPT_CHECK_FINITE, int(bool(check_finite)))
+
+    # -- lifetime
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().dg_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- options and sizes
+    def set_option(self, key, value):
+        _check(lib().dg_set_option(self._h, int(key), int(value)), self._h)
+
+    @property
+    def state_len(self):
+        return int(lib().dg_state_len(self._h))
+
+    @property
+    def shape(self):
+        return (self.nlat, self.nlon, 3, self.nphi)
+
+    def _host(self, u):
+        u = np.ascontiguousarray(u, dtype=np.float64).reshape(-1)
+        if u.size != self.state_len:
+            raise ValueError(f"state has {u.size} values, expected {self.state_len}")
+        return u
+
+    # -- state
+    def set_state(self, u):
+        u = self._host(u)
+        _check(lib().dg_set_state(self._h, _ptr(u), u.size), self._h)
+
+    def get_state(self):
+        out = np.empty(self.state_len)
+        _check(lib().dg_get_state(self._h, _ptr(out), out.size), self._h)
+        return out.reshape(self.shape)
+
+    def set_state_device(self, t):
+        """t: contiguous float64 CUDA tensor with state_len values."""
+        assert t.dtype.itemsize == 8 and t.is_contiguous() and t.numel() == self.state_len
+        _check(lib().dg_set_state_device(self._h, ctypes.c_void_p(t.data_ptr()), t.numel()), self._h)
+
+    def get_state_device(self, t):
+        assert t.dtype.itemsize == 8 and t.is_contiguous() and t.numel() == self.state_len
+        _check(lib().dg_get_state_device(self._h, ctypes.c_void_p(t.data_ptr()), t.numel()), self._h)
+
+    def get_time(self):
+        t = ctypes.c_double()
+        _check(lib().dg_get_time(self._h, ctypes.byref(t)), self._h)
+        return t.value
+
+    def set_time(self, t):
+        _check(lib().dg_set_time(self._h, float(t)), self._h)
+
+    # -- the method
+    def rhs(self, u):
+        u = self._host(u)
+        out = np.empty_like(u)
+        _check(lib().dg_rhs(self._h, _ptr(u), _ptr(out), u.size), self._h)
+        return out.reshape(self.shape)
+
+    def step(self, n, dt):
+        _check(lib().dg_step(self._h, int(n), float(dt)), self._h)
+
+    def total_mass(self):
+        m = ctypes.c_double()
+        _check(lib().dg_total_mass(self._h, ctypes.byref(m)), self._h)
+        return m.value
+
+    def total_mass_device(self, t):
+        """Enqueue the mass reduction; writes one float64 into CUDA tensor t."""
+        _check(lib().dg_total_mass_device(self._h, ctypes.c_void_p(t.data_ptr())), self._h)
+
+    def max_dt(self, cfl):
+        dt = ctypes.c_double()
+        _check(lib().dg_max_dt(self._h, float(cfl), ctypes.byref(dt)), self._h)
+        return dt.value
+
+    def stage_launches(self):
+        return int(lib().dg_stage_launches(self._h))
+
+    # -- projection of point values
+    def projection_nodes(self):
+        lam = np.empty(self.nlon * self.nm)
+        th = np.empty(self.nlat * self.nm)
+        _check(lib().dg_projection_nodes(self._h, _ptr(lam), lam.size, _ptr(th), th.size), self._h)
+        return lam, th
+
+    def project_nodal(self, vals):
+        v = np.ascontiguousarray(vals, dtype=np.float64).reshape(-1)
+        out = np.empty(self.state_len)
+        _check(lib().dg_project_nodal(self._h, _ptr(v), v.size, _ptr(out), out.size), self._h)
+        return out.reshape(self.shape)
+
+    def project_grid(self, fn_grid):
+        """Project fields given on the tensor grid of projection nodes:
+        fn_grid(lam1, th1) -> 3 arrays shaped [len(th1), len(lam1)]."""
+        lam, th = self.projection_nodes()
+        nm = self.nm
+        vals = [np.asarray(v, dtype=np.float64).reshape(self.nlat, nm, self.nlon, nm).transpose(0, 2, 1, 3)
+                for v in fn_grid(lam, th)]
+        return self.project_nodal(np.ascontiguousarray(np.stack(vals, axis=2)))

@@ -415,3 +415,14 @@ def test_planar_advection_rates_match_paper():
         rate = math.log2(e20 / e40)
         paper = math.log2(g[("gt4py", p, 20)] / g[("gt4py", p, 40)])
         assert abs(rate - (p + 1)) < 0.3 and abs(rate - paper) < 0.3, (p, rate, paper)
+
+
+def test_rhs_magnitude_bounds_the_tendency():
+    """The magnitude bound is >= |tendency| (triangle inequality) and equals it
+    for a single-term case (p = 0 rest state: only the pressure terms)."""
+    o = sphere(12, 6, 2)
+    u = o.project_tensor(synth.SmoothField(5).fields_grid)
+    k = o.rhs(u)
+    s = o.rhs_magnitude(u)
+    assert (s >= np.abs(k) * (1 - 1e-14)).all()
+    assert (s > 0).any()

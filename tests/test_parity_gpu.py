@@ -1,0 +1,245 @@
+"""Parity of the CUDA path (through the C-ABI) with the FP64 CPU oracle.
+
+Tolerances (per field, FP64 / FP32): 1e-12 / 1e-5.
+* States (projection, time stepping): relative to the reference field,
+  ||x - y||_2 / ||y||_2 and max|x - y| / max|y|.
+* Tendencies (dg_rhs): relative to the oracle's magnitude bound
+  S = |M^-1| sum |terms|.  The tendency of this mesh is a small difference of
+  large terms (flux divergences of a nearly non-divergent flow, amplified by
+  1/cos(theta) in the polar rows), so any floating-point evaluation of it is
+  only determined up to a few units of roundoff times S; two correct FP64
+  evaluations differ by ~1e-10 relative to the tendency itself.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2303_11767_gb300 import dgswe, synth
+
+pytestmark = pytest.mark.gpu
+
+R, G, OMEGA = synth.EARTH_RADIUS, 9.80616, 7.292e-5
+TOL = {"fp64": 1e-12, "fp32": 1e-5}
+NTHREADS = os.cpu_count() or 1
+
+
+def oracle_sphere(nlon, nlat, p):
+    o = O.Oracle.sphere(nlon, nlat, p, R, G, OMEGA)
+    o.set_threads(NTHREADS)
+    return o
+
+
+_cache = {}
+
+
+def case(nlon, nlat, p, seed):
+    """Oracle and the oracle-projected seeded state (cached)."""
+    key = (nlon, nlat, p, seed)
+    if key not in _cache:
+        o = oracle_sphere(nlon, nlat, p)
+        _cache[key] = (o, o.project_tensor(synth.SmoothField(seed).fields_grid))
+    return _cache[key]
+
+
+def state_err(x, y):
+    x = np.asarray(x).reshape(y.shape)
+    out = []
+    for f in range(3):
+        d = x[..., f, :] - y[..., f, :]
+        out.append((np.linalg.norm(d) / np.linalg.norm(y[..., f, :]), np.abs(d).max() / np.abs(y[..., f, :]).max()))
+    return out
+
+
+def tend_err(x, y, S):
+    x = np.asarray(x).reshape(y.shape)
+    out = []
+    for f in range(3):
+        d = x[..., f, :] - y[..., f, :]
+        out.append((np.linalg.norm(d) / np.linalg.norm(S[..., f, :]), np.abs(d).max() / S[..., f, :].max()))
+    return out
+
+
+def assert_within(errs, tol, what):
+    for f, (l2, mx) in enumerate(errs):
+        assert l2 <= tol and mx <= tol, f"{what}: field {f} l2={l2:.3e} max={mx:.3e} tol={tol:g}"
+
+
+def solver(nlon, nlat, p, prec, **kw):
+    return dgswe.Solver(nlon, nlat, p, R, G, OMEGA, precision=prec, **kw)
+
+
+# -------------------------------------------------------------- tendencies --
+
+# meshes spanning several tiles (a warp holds 32/(p+1) elements of a row, a
+# block 8 rows) with ragged last tiles, and degenerate tiny meshes
+SMALL = [(p, nlon, 19) for p, nlon in ((0, 67), (1, 35), (2, 23), (3, 19), (4, 15))] + \
+        [(p, 4, 2) for p in range(5)] + [(2, 1, 3), (3, 2, 9)]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("p,nlon,nlat", SMALL)
+def test_rhs_parity_small_meshes(p, nlon, nlat, prec):
+    o, u = case(nlon, nlat, p, 11)
+    with solver(nlon, nlat, p, prec) as s:
+        k = s.rhs(u)
+    assert_within(tend_err(k, o.rhs(u), o.rhs_magnitude(u)), TOL[prec], f"rhs p={p} {nlon}x{nlat} {prec}")
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("nlon,nlat,p,seed", [(20, 10, 1, 1), (180, 90, 3, 2), (360, 180, 4, 3)])
+def test_rhs_parity_configs(nlon, nlat, p, seed, prec):
+    o, u = case(nlon, nlat, p, seed)
+    with solver(nlon, nlat, p, prec) as s:
+        k = s.rhs(u)
+    assert_within(tend_err(k, o.rhs(u), o.rhs_magnitude(u)), TOL[prec], f"rhs {nlon}x{nlat} p={p} {prec}")
+
+
+# -------------------------------------------------------------- time steps --
+
+def _oracle_run(nlon, nlat, p, seed, nsteps, order=3, cfl=0.1):
+    key = ("run", nlon, nlat, p, seed, nsteps, order, cfl)
+    if key not in _cache:
+        o, u = case(nlon, nlat, p, seed)
+        dt = o.max_dt(u, cfl)
+        _cache[key] = (dt, o.total_mass(u), o.step(u, nsteps, dt, order))
+    return _cache[key]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("nlon,nlat,p,seed,nsteps", [(20, 10, 1, 1, 100), (180, 90, 3, 2, 1000)])
+def test_step_parity_and_mass(nlon, nlat, p, seed, nsteps, prec):
+    o, u = case(nlon, nlat, p, seed)
+    dt, m0, want = _oracle_run(nlon, nlat, p, seed, nsteps)
+    with solver(nlon, nlat, p, prec) as s:
+        s.set_state(u)
+        gm0 = s.total_mass()
+        s.step(nsteps, dt)
+        got = s.get_state()
+        gm1 = s.total_mass()
+        assert s.get_time() == pytest.approx(nsteps * dt, rel=1e-15)
+    assert_within(state_err(got, want), TOL[prec], f"{nsteps} steps {nlon}x{nlat} {prec}")
+    assert abs(gm0 / m0 - 1) < (1e-14 if prec == "fp64" else 1e-7)
+    assert abs(gm1 / gm0 - 1) < (1e-13 if prec == "fp64" else 1e-9), (gm0, gm1)
+
+
+@pytest.mark.parametrize("order", [1, 2, 3, 4])
+def test_rk_orders(order):
+    nlon, nlat, p = 16, 8, 2
+    o, u = case(nlon, nlat, p, 5)
+    dt = o.max_dt(u, 0.1)
+    want = o.step(u, 13, dt, order)
+    with solver(nlon, nlat, p, "fp64", rk_order=order) as s:
+        s.set_option(dgswe.OPT_STEPS_PER_GRAPH, 4)   # graphs of 4 steps plus a remainder
+        s.set_state(u)
+        s.step(13, dt)
+        assert_within(state_err(s.get_state(), want), 1e-12, f"RK{order}")
+
+
+# ------------------------------------------------------------- diagnostics --
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_max_dt_and_mass_match_oracle(prec):
+    nlon, nlat, p = 36, 18, 3
+    o, u = case(nlon, nlat, p, 6)
+    with solver(nlon, nlat, p, prec) as s:
+        s.set_state(u)
+        assert s.max_dt(0.1) == pytest.approx(o.max_dt(u, 0.1), rel=1e-12 if prec == "fp64" else 1e-6)
+        assert s.total_mass() == pytest.approx(o.total_mass(u), rel=1e-14 if prec == "fp64" else 1e-8)
+
+
+@pytest.mark.parametrize("nlon,nlat,p", [(20, 10, 1), (12, 7, 4)])
+def test_project_nodal_matches_oracle(nlon, nlat, p):
+    o = oracle_sphere(nlon, nlat, p)
+    f = synth.SmoothField(9)
+    want = o.project_tensor(f.fields_grid)
+    with solver(nlon, nlat, p, "fp64") as s:
+        got = s.project_grid(f.fields_grid)
+    assert_within(state_err(got, want), 1e-13, "projection")
+
+
+# -------------------------------------------------------- API and failures --
+
+def test_roundtrip_resume_and_determinism_fp64():
+    nlon, nlat, p = 24, 12, 2
+    o, u = case(nlon, nlat, p, 7)
+    dt = o.max_dt(u, 0.1)
+    with solver(nlon, nlat, p, "fp64") as s:
+        s.set_state(u)
+        np.testing.assert_array_equal(s.get_state(), u)     # FP64 resident state is the input
+        s.step(20, dt)
+        a = s.get_state()
+        s.set_state(u)
+        s.step(10, dt)
+        mid = s.get_state()
+        s.set_state(mid)
+        s.step(10, dt)
+        np.testing.assert_array_equal(s.get_state(), a)     # bitwise resume
+        launches = s.stage_launches()
+    assert launches == 3 * 40 + 1 * 0
+
+
+def test_determinism_fp32():
+    nlon, nlat, p = 40, 20, 3
+    _, u = case(nlon, nlat, p, 8)
+    outs = []
+    for _ in range(2):
+        with solver(nlon, nlat, p, "fp32") as s:
+            s.set_state(u)
+            s.step(25, 1.0)
+            outs.append((s.get_state(), s.total_mass()))
+    np.testing.assert_array_equal(outs[0][0], outs[1][0])
+    assert outs[0][1] == outs[1][1]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_nonphysical_and_nonfinite_are_reported(prec):
+    nlon, nlat, p = 16, 8, 1
+    _, u = case(nlon, nlat, p, 4)
+    bad = u.copy()
+    bad[3, 5, 0, 0] = -100.0                  # negative depth in one element
+    with solver(nlon, nlat, p, prec) as s:
+        with pytest.raises(dgswe.DGError) as e:
+            s.rhs(bad)
+        assert e.value.status == dgswe.DG_ENONPHYSICAL
+        nan = u.copy()
+        nan[2, 2, 1, 1] = np.nan              # NaN in a momentum mode
+        with pytest.raises(dgswe.DGError) as e:
+            s.rhs(nan)
+        assert e.value.status == dgswe.DG_ENONFINITE
+        s.set_state(nan)
+        with pytest.raises(dgswe.DGError) as e:
+            s.step(1, 1.0)
+        assert e.value.status == dgswe.DG_ENONFINITE
+        # the solver stays usable after a reported failure
+        s.set_state(u)
+        s.step(2, 1.0)
+        assert np.isfinite(s.get_state()).all()
+
+
+def test_option_errors():
+    with solver(8, 4, 1, "fp64") as s:
+        for key, val, status in [(dgswe.OPT_PRECISION, 2, dgswe.DG_EUNSUPPORTED),
+                                 (dgswe.OPT_ALPHA_MODE, 1, dgswe.DG_EUNSUPPORTED),
+                                 (dgswe.OPT_RK_ORDER, 5, dgswe.DG_EINVAL),
+                                 (99, 0, dgswe.DG_EINVAL)]:
+            with pytest.raises(dgswe.DGError) as e:
+                s.set_option(key, val)
+            assert e.value.status == status
+        with pytest.raises(dgswe.DGError):
+            s.step(1, 1.0)                    # no state yet
+        with pytest.raises(ValueError):
+            s.set_state(np.zeros(5))
+
+
+def test_precision_switch_keeps_state():
+    nlon, nlat, p = 20, 10, 1
+    _, u = case(nlon, nlat, p, 1)
+    with solver(nlon, nlat, p, "fp64") as s:
+        s.set_state(u)
+        s.set_option(dgswe.OPT_PRECISION, dgswe.PREC["fp32"])
+        assert_within(state_err(s.get_state(), u), 1e-7, "to fp32")
+        s.set_option(dgswe.OPT_PRECISION, dgswe.PREC["fp64"])
+        assert_within(state_err(s.get_state(), u), 1e-7, "back to fp64")
