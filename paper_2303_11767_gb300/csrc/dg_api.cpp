@@ -75,9 +75,12 @@ struct dg_ctx {
     // options
     int prec = DG_PREC_FP64, rk = 3, check = 1, alpha_mode = 0, spg = 16;
     cudaStream_t own_stream = nullptr, stream = nullptr;
-    // device buffers
-    void *U[4] = {nullptr, nullptr, nullptr, nullptr};   // state buffers of the active precision
-    int cur = 0;                                          // buffer holding the state
+    // device buffers of the active precision (increment-form time stepping)
+    void *B[2] = {nullptr, nullptr};   // u^n, ping-pong: the last stage writes the other one
+    void *L[2] = {nullptr, nullptr};   // low parts of u^n (FP32 path only)
+    void *I[2] = {nullptr, nullptr};   // stage increments u_s - u^n
+    void *D = nullptr;                 // RK4 accumulator
+    int cur = 0;                       // index of B / L holding u^n
     double *stage64 = nullptr;                            // FP64 staging of one state
     RowTab<double> *rows64 = nullptr;
     RowTab<float> *rows32 = nullptr;
@@ -108,17 +111,23 @@ void drop_graphs(dg_ctx *h)
 
 void free_state_buffers(dg_ctx *h)
 {
-    for (auto &u : h->U) {
-        if (u) cudaFree(u);
-        u = nullptr;
+    void **all[] = {&h->B[0], &h->B[1], &h->L[0], &h->L[1], &h->I[0], &h->I[1], &h->D};
+    for (void **u : all) {
+        if (*u) cudaFree(*u);
+        *u = nullptr;
     }
 }
 
 dg_status alloc_state_buffers(dg_ctx *h)
 {
     const size_t bytes = h->len * elem_size(h->prec);
-    for (auto &u : h->U) {
-        if (cudaMalloc(&u, bytes) != cudaSuccess) {
+    std::vector<void **> want = {&h->B[0], &h->B[1], &h->I[0], &h->I[1], &h->D};
+    if (h->prec == DG_PREC_FP32) {
+        want.push_back(&h->L[0]);
+        want.push_back(&h->L[1]);
+    }
+    for (void **u : want) {
+        if (cudaMalloc(u, bytes) != cudaSuccess) {
             free_state_buffers(h);
             return fail(DG_ENOMEM, "cudaMalloc of %zu bytes failed", bytes);
         }
@@ -146,35 +155,39 @@ StageArgs<T> base_args(dg_ctx *h, const RowTab<T> *rows, double href)
     return a;
 }
 
+// One stage of the increment-form RK step.  inc_in / inc_out index I[],
+// -1 = none; acc_in / acc_out use D; fin = last stage (updates u^n into the
+// other base buffer).
 struct StagePlan {
-    int in, P, out, P2, out2;   // buffer indices, -1 = none
-    double ca, cb, cc, ca2, cc2;
+    int inc_in, inc_out, acc_in, acc_out, fin;
+    double ci, ca, cc, cd;
 };
 
-// The explicit RK schemes of Table "Butcher" in low-storage form.  Buffer
-// indices are relative: 0 is the buffer holding u^n.
-int rk_plan(int order, StagePlan *pl, int *flips)
+// The explicit RK schemes of Table "Butcher" in increment form: every stage
+// state is u^n + inc, and the last stage adds
+//   u^{n+1} - u^n = sum_s b_s dt k_s
+// to u^n once, with a two-sum.  SSP RK3: inc1 = dt k1, inc2 = (inc1 + dt k2)/4,
+// u^{n+1} = u^n + 2/3 (inc2 + dt k3) (the Shu-Osher stages minus u^n).
+int rk_plan(int order, StagePlan *pl)
 {
-    *flips = 0;
     switch (order) {
-    case 1:   // u1 = u + dt k(u); the result lives in the other buffer
-        pl[0] = {0, -1, 1, -1, -1, 0, 1, 1, 0, 0};
-        *flips = 1;
+    case 1:
+        pl[0] = {-1, -1, -1, -1, 1, 0, 0, 1, 0};
         return 1;
-    case 2:   // u1 = u + dt k(u); u = u/2 + (u1 + dt k(u1))/2
-        pl[0] = {0, -1, 1, -1, -1, 0, 1, 1, 0, 0};
-        pl[1] = {1, 0, 0, -1, -1, 0.5, 0.5, 0.5, 0, 0};
+    case 2:
+        pl[0] = {-1, 0, -1, -1, 0, 0, 0, 1, 0};
+        pl[1] = {0, -1, -1, -1, 1, 0.5, 0, 0.5, 0};
         return 2;
-    case 3:   // Shu-Osher form of the SSP RK3 tableau
-        pl[0] = {0, -1, 1, -1, -1, 0, 1, 1, 0, 0};
-        pl[1] = {1, 0, 2, -1, -1, 0.75, 0.25, 0.25, 0, 0};
-        pl[2] = {2, 0, 0, -1, -1, 1.0 / 3.0, 2.0 / 3.0, 2.0 / 3.0, 0, 0};
+    case 3:
+        pl[0] = {-1, 0, -1, -1, 0, 0, 0, 1, 0};
+        pl[1] = {0, 1, -1, -1, 0, 0.25, 0, 0.25, 0};
+        pl[2] = {1, -1, -1, -1, 1, 2.0 / 3.0, 0, 2.0 / 3.0, 0};
         return 3;
-    case 4:   // classical RK4 tableau with an accumulator (buffer 3)
-        pl[0] = {0, -1, 1, 0, 3, 0, 1, 0.5, 1, 1.0 / 6.0};
-        pl[1] = {1, 0, 2, 3, 3, 1, 0, 0.5, 1, 1.0 / 3.0};
-        pl[2] = {2, 0, 1, 3, 3, 1, 0, 1.0, 1, 1.0 / 3.0};
-        pl[3] = {1, 3, 0, -1, -1, 1, 0, 1.0 / 6.0, 0, 0};
+    case 4:   // classical tableau: stages u + dt k1/2, u + dt k2/2, u + dt k3
+        pl[0] = {-1, 0, -1, 1, 0, 0, 1.0 / 6.0, 0.5, 0};
+        pl[1] = {0, 1, 1, 1, 0, 0, 1.0 / 3.0, 0.5, 0};
+        pl[2] = {1, 0, 1, 1, 0, 0, 1.0 / 3.0, 1.0, 0};
+        pl[3] = {0, -1, 1, -1, 1, 0, 0, 1.0 / 6.0, 1.0};
         return 4;
     default:
         return 0;
@@ -185,26 +198,24 @@ template <typename T>
 dg_status launch_step_t(dg_ctx *h, double dt, int cur, const RowTab<T> *rows)
 {
     StagePlan pl[4];
-    int flips = 0;
-    const int ns = rk_plan(h->rk, pl, &flips);
-    auto buf = [&](int rel) -> T * {
-        if (rel < 0) return nullptr;
-        int idx = rel;
-        if (rel <= 1) idx = rel ^ cur;   // buffers 0 and 1 swap roles for RK1 ping-pong
-        return static_cast<T *>(h->U[idx]);
-    };
+    const int ns = rk_plan(h->rk, pl);
+    auto I = [&](int i) -> T * { return i < 0 ? nullptr : static_cast<T *>(h->I[i]); };
     for (int s = 0; s < ns; ++s) {
         StageArgs<T> a = base_args<T>(h, rows, h->href);
-        a.u_in = buf(pl[s].in);
-        a.P = buf(pl[s].P);
-        a.out = buf(pl[s].out);
-        a.P2 = buf(pl[s].P2);
-        a.out2 = buf(pl[s].out2);
+        a.base = static_cast<const T *>(h->B[cur]);
+        a.inc = I(pl[s].inc_in);
+        a.inc_out = I(pl[s].inc_out);
+        a.acc_in = pl[s].acc_in >= 0 ? static_cast<const T *>(h->D) : nullptr;
+        a.acc_out = pl[s].acc_out >= 0 ? static_cast<T *>(h->D) : nullptr;
+        if (pl[s].fin) {
+            a.lo = static_cast<const T *>(h->L[cur]);
+            a.out_base = static_cast<T *>(h->B[cur ^ 1]);
+            a.out_lo = static_cast<T *>(h->L[cur ^ 1]);
+        }
+        a.ci = (T)pl[s].ci;
         a.ca = (T)pl[s].ca;
-        a.cb = (T)pl[s].cb;
         a.cc = (T)pl[s].cc;
-        a.ca2 = (T)pl[s].ca2;
-        a.cc2 = (T)pl[s].cc2;
+        a.cd = (T)pl[s].cd;
         a.dt = (T)dt;
         if (dg_launch_stage<T>(h->n, a, h->stream))
             return fail(DG_ECUDA, "stage kernel launch failed: %s", cudaGetErrorString(cudaGetLastError()));
@@ -219,7 +230,7 @@ dg_status launch_steps(dg_ctx *h, int nsteps, double dt, int *cur)
         dg_status st = h->prec == DG_PREC_FP64 ? launch_step_t<double>(h, dt, *cur, h->rows64)
                                                : launch_step_t<float>(h, dt, *cur, h->rows32);
         if (st) return st;
-        if (h->rk == 1) *cur ^= 1;
+        *cur ^= 1;   // u^{n+1} lives in the other base buffer
     }
     return DG_OK;
 }
@@ -296,20 +307,24 @@ double mean_depth(const double *modal, size_t nel, int nphi)
     return 0.5 * s / (double)nel;   // mode 0 of h times phi_0 = 1/2
 }
 
-dg_status to_internal(dg_ctx *h, const double *d_src, void *dst, double href)
+dg_status to_internal(dg_ctx *h, const double *d_src, void *dst, void *lo, double href)
 {
     int r = h->prec == DG_PREC_FP64
-                ? dg_launch_to_internal<double>(d_src, static_cast<double *>(dst), h->nel, h->nphi, href, h->stream)
-                : dg_launch_to_internal<float>(d_src, static_cast<float *>(dst), h->nel, h->nphi, href, h->stream);
+                ? dg_launch_to_internal<double>(d_src, static_cast<double *>(dst), static_cast<double *>(lo), h->nel,
+                                                h->nphi, href, h->stream)
+                : dg_launch_to_internal<float>(d_src, static_cast<float *>(dst), static_cast<float *>(lo), h->nel,
+                                               h->nphi, href, h->stream);
     if (r) return fail(DG_ECUDA, "conversion kernel failed: %s", cudaGetErrorString(cudaGetLastError()));
     return DG_OK;
 }
 
-dg_status to_api(dg_ctx *h, const void *src, double *d_dst, double href)
+dg_status to_api(dg_ctx *h, const void *src, const void *lo, double *d_dst, double href)
 {
     int r = h->prec == DG_PREC_FP64
-                ? dg_launch_to_api<double>(static_cast<const double *>(src), d_dst, h->nel, h->nphi, href, h->stream)
-                : dg_launch_to_api<float>(static_cast<const float *>(src), d_dst, h->nel, h->nphi, href, h->stream);
+                ? dg_launch_to_api<double>(static_cast<const double *>(src), static_cast<const double *>(lo), d_dst,
+                                           h->nel, h->nphi, href, h->stream)
+                : dg_launch_to_api<float>(static_cast<const float *>(src), static_cast<const float *>(lo), d_dst,
+                                          h->nel, h->nphi, href, h->stream);
     if (r) return fail(DG_ECUDA, "conversion kernel failed: %s", cudaGetErrorString(cudaGetLastError()));
     return DG_OK;
 }
@@ -452,7 +467,7 @@ dg_status dg_set_option(dg_handle h, int key, long long value)
         CUDA_TRY(cudaStreamSynchronize(h->stream));
         // carry the resident state over through the FP64 staging buffer
         if (h->have_state) {
-            if (dg_status s = to_api(h, h->U[h->cur], h->stage64, h->href)) return s;
+            if (dg_status s = to_api(h, h->B[h->cur], h->L[h->cur], h->stage64, h->href)) return s;
             CUDA_TRY(cudaStreamSynchronize(h->stream));
         }
         drop_graphs(h);
@@ -472,7 +487,7 @@ dg_status dg_set_option(dg_handle h, int key, long long value)
             } else {
                 h->href = 0.0;
             }
-            if (dg_status s = to_internal(h, h->stage64, h->U[0], h->href)) return s;
+            if (dg_status s = to_internal(h, h->stage64, h->B[0], h->L[0], h->href)) return s;
             CUDA_TRY(cudaStreamSynchronize(h->stream));
         }
         return DG_OK;
@@ -522,7 +537,7 @@ dg_status dg_set_state_device(dg_handle h, const double *d_modal, size_t len)
         h->href = 0.5 * s / (double)h->nel;
     }
     h->cur = 0;
-    if (dg_status s = to_internal(h, h->stage64, h->U[0], h->href)) return s;
+    if (dg_status s = to_internal(h, h->stage64, h->B[0], h->L[0], h->href)) return s;
     h->have_state = true;
     return DG_OK;
 }
@@ -535,7 +550,7 @@ dg_status dg_set_state(dg_handle h, const double *modal, size_t len)
     CUDA_TRY(cudaMemcpyAsync(h->stage64, modal, len * sizeof(double), cudaMemcpyHostToDevice, h->stream));
     h->href = h->prec == DG_PREC_FP32 ? mean_depth(modal, h->nel, h->nphi) : 0.0;
     h->cur = 0;
-    if (dg_status s = to_internal(h, h->stage64, h->U[0], h->href)) return s;
+    if (dg_status s = to_internal(h, h->stage64, h->B[0], h->L[0], h->href)) return s;
     CUDA_TRY(cudaStreamSynchronize(h->stream));   // the host buffer is only borrowed
     h->have_state = true;
     return DG_OK;
@@ -547,7 +562,7 @@ dg_status dg_get_state_device(dg_handle h, double *d_modal, size_t len)
     if (!d_modal || len != h->len) return fail(DG_EINVAL, "state length %zu, expected %zu", len, h->len);
     if (!h->have_state) return fail(DG_EINVAL, "no state set");
     DeviceGuard dg(h->device);
-    return to_api(h, h->U[h->cur], d_modal, h->href);
+    return to_api(h, h->B[h->cur], h->L[h->cur], d_modal, h->href);
 }
 
 dg_status dg_get_state(dg_handle h, double *modal, size_t len)
@@ -556,7 +571,7 @@ dg_status dg_get_state(dg_handle h, double *modal, size_t len)
     if (!modal || len != h->len) return fail(DG_EINVAL, "state length %zu, expected %zu", len, h->len);
     if (!h->have_state) return fail(DG_EINVAL, "no state set");
     DeviceGuard dg(h->device);
-    if (dg_status s = to_api(h, h->U[h->cur], h->stage64, h->href)) return s;
+    if (dg_status s = to_api(h, h->B[h->cur], h->L[h->cur], h->stage64, h->href)) return s;
     CUDA_TRY(cudaMemcpyAsync(modal, h->stage64, len * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     CUDA_TRY(cudaStreamSynchronize(h->stream));
     return DG_OK;
@@ -567,30 +582,26 @@ dg_status dg_rhs(dg_handle h, const double *modal_in, double *tend_out, size_t l
     if (dg_status s = check(h)) return s;
     if (!modal_in || !tend_out || len != h->len) return fail(DG_EINVAL, "state length %zu, expected %zu", len, h->len);
     DeviceGuard dg(h->device);
-    // scratch: every buffer but U[cur] is free between steps (cur is 0 or 1)
-    void *in = h->U[h->cur ^ 1], *outb = h->U[2];
+    // scratch: the increment buffers are free between steps
+    void *in = h->I[0], *outb = h->I[1];
     const double href = h->prec == DG_PREC_FP32 ? mean_depth(modal_in, h->nel, h->nphi) : 0.0;
     CUDA_TRY(cudaMemcpyAsync(h->stage64, modal_in, len * sizeof(double), cudaMemcpyHostToDevice, h->stream));
-    if (dg_status s = to_internal(h, h->stage64, in, href)) return s;
+    if (dg_status s = to_internal(h, h->stage64, in, nullptr, href)) return s;
     int r;
     if (h->prec == DG_PREC_FP64) {
         StageArgs<double> a = base_args<double>(h, h->rows64, href);
-        a.u_in = static_cast<double *>(in);
-        a.out = static_cast<double *>(outb);
-        a.cc = 1.0;
-        a.dt = 1.0;
+        a.base = static_cast<double *>(in);
+        a.out_rhs = static_cast<double *>(outb);
         r = dg_launch_stage<double>(h->n, a, h->stream);
     } else {
         StageArgs<float> a = base_args<float>(h, h->rows32, href);
-        a.u_in = static_cast<float *>(in);
-        a.out = static_cast<float *>(outb);
-        a.cc = 1.0f;
-        a.dt = 1.0f;
+        a.base = static_cast<float *>(in);
+        a.out_rhs = static_cast<float *>(outb);
         r = dg_launch_stage<float>(h->n, a, h->stream);
     }
     if (r) return fail(DG_ECUDA, "stage kernel launch failed: %s", cudaGetErrorString(cudaGetLastError()));
     h->launches++;
-    if (dg_status s = to_api(h, outb, h->stage64, 0.0)) return s;   // tendencies carry no reference depth
+    if (dg_status s = to_api(h, outb, nullptr, h->stage64, 0.0)) return s;   // tendencies carry no reference depth
     CUDA_TRY(cudaMemcpyAsync(tend_out, h->stage64, len * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     CUDA_TRY(cudaStreamSynchronize(h->stream));
     if (h->check) return read_status(h);
@@ -606,7 +617,7 @@ dg_status dg_step(dg_handle h, int n, double dt)
     if (n == 0) return DG_OK;
     DeviceGuard dg(h->device);
     int K = std::min(h->spg, n);
-    if (h->rk == 1 && (K & 1) && K > 1) K -= 1;   // keep the ping-pong even inside a graph
+    if ((K & 1) && K > 1) K -= 1;   // even graphs return u^n to the same base buffer
     int full = n / K, rest = n - full * K;
     if (full > 0) {
         GraphEntry *ge = nullptr;
@@ -646,8 +657,7 @@ dg_status dg_step(dg_handle h, int n, double dt)
             ge = &h->graphs.back();
         }
         StagePlan pl[4];
-        int flips;
-        const int ns = rk_plan(h->rk, pl, &flips);
+        const int ns = rk_plan(h->rk, pl);
         for (int r = 0; r < full; ++r) {
             CUDA_TRY(cudaGraphLaunch(ge->exec, h->stream));
             h->launches += (long long)K * ns;
@@ -670,10 +680,12 @@ namespace {
 dg_status enqueue_mass(dg_ctx *h, double *d_out)
 {
     int r = h->prec == DG_PREC_FP64
-                ? dg_launch_mass<double>(static_cast<const double *>(h->U[h->cur]), h->c0, h->nlon, h->nlat, h->n,
+                ? dg_launch_mass<double>(static_cast<const double *>(h->B[h->cur]),
+                                         static_cast<const double *>(h->L[h->cur]), h->c0, h->nlon, h->nlat, h->n,
                                          h->href, h->tab.dlam, h->tab.dth, h->R * h->R, h->partials, h->nblocks,
                                          d_out, h->stream)
-                : dg_launch_mass<float>(static_cast<const float *>(h->U[h->cur]), h->c0, h->nlon, h->nlat, h->n,
+                : dg_launch_mass<float>(static_cast<const float *>(h->B[h->cur]),
+                                        static_cast<const float *>(h->L[h->cur]), h->c0, h->nlon, h->nlat, h->n,
                                         h->href, h->tab.dlam, h->tab.dth, h->R * h->R, h->partials, h->nblocks,
                                         d_out, h->stream);
     if (r) return fail(DG_ECUDA, "mass kernel failed: %s", cudaGetErrorString(cudaGetLastError()));
@@ -715,9 +727,9 @@ dg_status dg_max_dt(dg_handle h, double cfl, double *dt)
     DeviceGuard dg(h->device);
     CUDA_TRY(cudaMemsetAsync(h->d_maxbits, 0, sizeof(unsigned long long), h->stream));
     int r = h->prec == DG_PREC_FP64
-                ? dg_launch_max_speed<double>(static_cast<const double *>(h->U[h->cur]), h->nlon, h->nlat, h->n,
+                ? dg_launch_max_speed<double>(static_cast<const double *>(h->B[h->cur]), h->nlon, h->nlat, h->n,
                                               h->href, h->g, h->d_maxbits, h->d_status, h->stream)
-                : dg_launch_max_speed<float>(static_cast<const float *>(h->U[h->cur]), h->nlon, h->nlat, h->n,
+                : dg_launch_max_speed<float>(static_cast<const float *>(h->B[h->cur]), h->nlon, h->nlat, h->n,
                                              h->href, h->g, h->d_maxbits, h->d_status, h->stream);
     if (r) return fail(DG_ECUDA, "wave-speed kernel failed: %s", cudaGetErrorString(cudaGetLastError()));
     unsigned long long bits = 0;

@@ -54,24 +54,34 @@ double dg_legendre_deriv(int k, double x);
 int dg_build_tables(HostTables &t, int nlon, int nlat, int p, double R, double g);
 void dg_free_tables(HostTables &t);
 
-// Stage-kernel launch description (dg_stage.cu).  One fused kernel computes
-// k = M^{-1} h(u_in) and writes
-//   out  = ca * P  + cb * u_in + cc * dt * k        (P may be null when ca == 0)
-//   out2 = ca2 * P2 + cc2 * dt * k                  (optional second output)
+// Stage-kernel launch description.  The time integration is written in
+// increment form: the state u^n is held as (base, lo) -- lo carries the bits
+// that do not fit into base (FP32 path; null in FP64) -- and every stage
+// state is u^n + inc.  One fused kernel computes k = M^{-1} h(u_stage),
+// u_stage = base + inc (inc may be null), and then, as requested:
+//   out_rhs  = k                                              (tendency only)
+//   inc_out  = ci * inc + cc * dt * k                         (next increment)
+//   acc_out  = acc_in + ca * dt * k                           (RK4 accumulator)
+//   (out_base, out_lo) = (base, lo) + ci * inc + cd * acc_in + cc * dt * k
+//                         (final stage, error-free two-sum update of u^n)
 template <typename T>
 struct StageArgs {
-    const T *u_in;
-    const T *P;
-    T *out;
-    const T *P2;
-    T *out2;
+    const T *base;
+    const T *inc;
+    const T *lo;
+    const T *acc_in;
+    T *out_rhs;
+    T *inc_out;
+    T *acc_out;
+    T *out_base;
+    T *out_lo;
     const RowTab<T> *rows;
     unsigned int *status;
     int nlon, nlat;
     T href;          // reference depth: h = href + stored h
     T P0;            // g href^2 / 2 (pressure carried by the rho table)
     T g, cF, cG, invR, twoOmega;
-    T ca, cb, cc, ca2, cc2, dt;
+    T ci, ca, cc, cd, dt;
 };
 
 // status bits written by device code
@@ -84,13 +94,16 @@ template <typename T>
 int dg_upload_basis(const BasisTab<double> *all);   // all[n-1] for n = 1..DG_MAXN
 
 // dg_aux.cu
+// FP64 API layout <-> internal (base, lo) with h stored relative to href; lo
+// may be null (FP64 path).
 template <typename T>
-int dg_launch_to_internal(const double *src, T *dst, size_t nel, int nphi, double href, void *stream);
+int dg_launch_to_internal(const double *src, T *dst, T *lo, size_t nel, int nphi, double href, void *stream);
 template <typename T>
-int dg_launch_to_api(const T *src, double *dst, size_t nel, int nphi, double href, void *stream);
+int dg_launch_to_api(const T *src, const T *lo, double *dst, size_t nel, int nphi, double href, void *stream);
 template <typename T>
-int dg_launch_mass(const T *u, const double *c0, int nlon, int nlat, int n, double href, double dlam,
-                   double dth, double scale, double *partials, int nblocks, double *result, void *stream);
+int dg_launch_mass(const T *u, const T *lo, const double *c0, int nlon, int nlat, int n, double href,
+                   double dlam, double dth, double scale, double *partials, int nblocks, double *result,
+                   void *stream);
 template <typename T>
 int dg_launch_max_speed(const T *u, int nlon, int nlat, int n, double href, double g,
                         unsigned long long *maxbits, unsigned int *status, void *stream);

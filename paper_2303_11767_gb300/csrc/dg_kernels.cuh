@@ -59,6 +59,13 @@ struct Geo {
 template <typename T>
 __device__ __forceinline__ T rcp(T x) { return T(1) / x; }
 
+// h <= 0 makes u = hu/h meaningless; a NaN depth is reported as non-finite.
+template <typename T>
+__device__ __forceinline__ void check_depth(T h, unsigned &st)
+{
+    if (!(h > T(0))) st |= (h != h) ? DG_STATUS_NONFINITE : DG_STATUS_NONPHYSICAL;
+}
+
 // Physical lambda-flux (hu, hu u + P, hu v) of a state q = (h', hu, hv) with
 // h = href + h' and the pressure P = g h' (href + h'/2) (the constant part
 // g href^2/2 is carried by the rho table), and the wave speed |u| + sqrt(g h).
@@ -66,7 +73,7 @@ template <typename T>
 __device__ __forceinline__ void lam_flux(const T *q, T href, T g, T *f, T &speed, unsigned &st)
 {
     const T h = href + q[0];
-    if (!(h > T(0))) st |= DG_STATUS_NONPHYSICAL;
+    check_depth(h, st);
     const T u = q[1] * rcp(h);
     const T P = q[0] * g * (href + T(0.5) * q[0]);
     f[0] = q[1];
@@ -79,7 +86,7 @@ template <typename T>
 __device__ __forceinline__ void th_flux(const T *q, T href, T g, T *f, T &speed, unsigned &st)
 {
     const T h = href + q[0];
-    if (!(h > T(0))) st |= DG_STATUS_NONPHYSICAL;
+    check_depth(h, st);
     const T v = q[2] * rcp(h);
     const T P = q[0] * g * (href + T(0.5) * q[0]);
     f[0] = q[2];
@@ -184,6 +191,19 @@ __device__ __forceinline__ void store_row<double, 4>(double *p, const double *o)
     reinterpret_cast<double2 *>(p)[1] = make_double2(o[2], o[3]);
 }
 
+// Row of the stage state u_stage = base + inc (inc may be null).
+template <typename T, int N>
+__device__ __forceinline__ void load_stage_row(const T *__restrict__ base, const T *__restrict__ inc, size_t off, T *o)
+{
+    load_row<T, N>(base + off, o);
+    if (inc) {
+        T d[N];
+        load_row<T, N>(inc + off, d);
+#pragma unroll
+        for (int a = 0; a < N; ++a) o[a] += d[a];
+    }
+}
+
 template <typename T, int N>
 __global__ void __launch_bounds__(32 * DG_WARPS) stage_kernel(const StageArgs<T> A)
 {
@@ -215,7 +235,7 @@ __global__ void __launch_bounds__(32 * DG_WARPS) stage_kernel(const StageArgs<T>
     T uh[3][N];
 #pragma unroll
     for (int f = 0; f < 3; ++f) {
-        if (valid) load_row<T, N>(A.u_in + e * EL + f * NP + k * N, uh[f]);
+        if (valid) load_stage_row<T, N>(A.base, A.inc, e * EL + f * NP + k * N, uh[f]);
         else {
 #pragma unroll
             for (int a = 0; a < N; ++a) uh[f][a] = T(0);
@@ -316,7 +336,7 @@ __global__ void __launch_bounds__(32 * DG_WARPS) stage_kernel(const StageArgs<T>
                 side = north ? 2 : 3;           // north halo needs its S trace
                 sl = (north ? Wv + 1 : 0) * TW + c + 1;
             }
-            const T *src = A.u_in + ((size_t)he_j * A.nlon + he_i) * EL;
+            const size_t hoff = ((size_t)he_j * A.nlon + he_i) * EL;
             T *slot = trc + sl * TRC;
 #pragma unroll
             for (int f = 0; f < 3; ++f) {
@@ -325,7 +345,7 @@ __global__ void __launch_bounds__(32 * DG_WARPS) stage_kernel(const StageArgs<T>
 #pragma unroll
                     for (int b = 0; b < N; ++b) {
                         T row[N];
-                        load_row<T, N>(src + f * NP + b * N, row);
+                        load_stage_row<T, N>(A.base, A.inc, hoff + f * NP + b * N, row);
                         T s = T(0);
 #pragma unroll
                         for (int a = 0; a < N; ++a) s = fma(side == 1 ? B.SE[a] : B.SW[a], row[a], s);
@@ -335,7 +355,7 @@ __global__ void __launch_bounds__(32 * DG_WARPS) stage_kernel(const StageArgs<T>
 #pragma unroll
                     for (int b = 0; b < N; ++b) {
                         T row[N];
-                        load_row<T, N>(src + f * NP + b * N, row);
+                        load_stage_row<T, N>(A.base, A.inc, hoff + f * NP + b * N, row);
                         T s = T(0);
 #pragma unroll
                         for (int a = 0; a < N; ++a) s = fma(B.LV[a][kk], row[a], s);
@@ -393,7 +413,7 @@ __global__ void __launch_bounds__(32 * DG_WARPS) stage_kernel(const StageArgs<T>
         for (int q = 0; q < N; ++q) {
             const T hp = qn[0][q], hu = qn[1][q], hv = qn[2][q];
             const T h = href + hp;
-            if (!(h > T(0))) st |= DG_STATUS_NONPHYSICAL;
+            check_depth(h, st);
             const T rh = rcp(h);
             const T u = hu * rh, v = hv * rh;
             const T P = hp * gg * (href + T(0.5) * hp);
@@ -472,31 +492,62 @@ __global__ void __launch_bounds__(32 * DG_WARPS) stage_kernel(const StageArgs<T>
         kk[2][0] = fma(A.P0, rhok, kk[2][0]);
 
         if (valid) {
-            const T cdt = A.cc * A.dt;
+            const T cdt = A.cc * A.dt, adt = A.ca * A.dt;
 #pragma unroll
             for (int f = 0; f < 3; ++f) {
-                T o[N], pr[N];
-                if (A.ca != T(0)) load_row<T, N>(A.P + e * EL + f * NP + k * N, pr);
+                const size_t off = e * EL + f * NP + k * N;
+#pragma unroll
+                for (int a = 0; a < N; ++a)
+                    if (!isfinite(kk[f][a])) st |= DG_STATUS_NONFINITE;
+                if (A.out_rhs) store_row<T, N>(A.out_rhs + off, kk[f]);
+                T inc[N];
+                if (A.inc) load_row<T, N>(A.inc + off, inc);
                 else {
 #pragma unroll
-                    for (int a = 0; a < N; ++a) pr[a] = T(0);
+                    for (int a = 0; a < N; ++a) inc[a] = T(0);
                 }
+                if (A.inc_out) {
+                    T o[N];
 #pragma unroll
-                for (int a = 0; a < N; ++a) {
-                    o[a] = fma(cdt, kk[f][a], fma(A.cb, uh[f][a], A.ca * pr[a]));
-                    if (!isfinite(o[a])) st |= DG_STATUS_NONFINITE;
+                    for (int a = 0; a < N; ++a) o[a] = fma(cdt, kk[f][a], A.ci * inc[a]);
+                    store_row<T, N>(A.inc_out + off, o);
                 }
-                store_row<T, N>(A.out + e * EL + f * NP + k * N, o);
-            }
-            if (A.out2) {
-                const T cdt2 = A.cc2 * A.dt;
+                T acc[N];
+                if (A.acc_in) load_row<T, N>(A.acc_in + off, acc);
+                else {
 #pragma unroll
-                for (int f = 0; f < 3; ++f) {
-                    T o[N], pr[N];
-                    load_row<T, N>(A.P2 + e * EL + f * NP + k * N, pr);
+                    for (int a = 0; a < N; ++a) acc[a] = T(0);
+                }
+                if (A.acc_out) {
+                    T o[N];
 #pragma unroll
-                    for (int a = 0; a < N; ++a) o[a] = fma(cdt2, kk[f][a], A.ca2 * pr[a]);
-                    store_row<T, N>(A.out2 + e * EL + f * NP + k * N, o);
+                    for (int a = 0; a < N; ++a) o[a] = fma(adt, kk[f][a], acc[a]);
+                    store_row<T, N>(A.acc_out + off, o);
+                }
+                if (A.out_base) {
+                    // u^{n+1} = (base + lo) + delta with an error-free two-sum,
+                    // so increments far below one ulp of the state survive
+                    T bs[N], lo[N], ob[N], ol[N];
+                    load_row<T, N>(A.base + off, bs);
+                    if (A.lo) load_row<T, N>(A.lo + off, lo);
+                    else {
+#pragma unroll
+                        for (int a = 0; a < N; ++a) lo[a] = T(0);
+                    }
+#pragma unroll
+                    for (int a = 0; a < N; ++a) {
+                        const T delta = fma(cdt, kk[f][a], fma(A.cd, acc[a], A.ci * inc[a]));
+                        const T s1 = bs[a] + delta;
+                        const T bp = s1 - bs[a];
+                        const T err = (bs[a] - (s1 - bp)) + (delta - bp);
+                        const T l1 = lo[a] + err;
+                        const T hi = s1 + l1;
+                        ob[a] = hi;
+                        ol[a] = l1 - (hi - s1);
+                        if (!isfinite(hi)) st |= DG_STATUS_NONFINITE;
+                    }
+                    store_row<T, N>(A.out_base + off, ob);
+                    if (A.out_lo) store_row<T, N>(A.out_lo + off, ol);
                 }
             }
         }
@@ -533,25 +584,28 @@ int launch_stage_n(const StageArgs<T> &a, cudaStream_t s)
 
 // ------------------------------------------------------------- auxiliary --
 
-// API layout (FP64, full h) <-> internal layout (T, h stored relative to href).
+// API layout (FP64, full h) <-> internal (base, lo) layout with h stored
+// relative to href.  lo receives what base (T) cannot hold; may be null.
 template <typename T>
-__global__ void to_internal_kernel(const double *__restrict__ src, T *__restrict__ dst, size_t nval, int per_el,
-                                   int nphi, double href)
+__global__ void to_internal_kernel(const double *__restrict__ src, T *__restrict__ dst, T *__restrict__ lo,
+                                   size_t nval, int per_el, double href)
 {
     for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < nval; t += (size_t)gridDim.x * blockDim.x) {
         double v = src[t];
         if (t % per_el == 0) v -= 2.0 * href;   // mode 0 of h: phi_0 = 1/2
-        dst[t] = (T)v;
+        const T hi = (T)v;
+        dst[t] = hi;
+        if (lo) lo[t] = (T)(v - (double)hi);
     }
-    (void)nphi;
 }
 
 template <typename T>
-__global__ void to_api_kernel(const T *__restrict__ src, double *__restrict__ dst, size_t nval, int per_el,
-                              double href)
+__global__ void to_api_kernel(const T *__restrict__ src, const T *__restrict__ lo, double *__restrict__ dst,
+                              size_t nval, int per_el, double href)
 {
     for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < nval; t += (size_t)gridDim.x * blockDim.x) {
         double v = (double)src[t];
+        if (lo) v += (double)lo[t];
         if (t % per_el == 0) v += 2.0 * href;
         dst[t] = v;
     }
@@ -586,6 +640,7 @@ constexpr int MASS_THREADS = 256;
 // c0: nlat * n values C_j[0][b]; area row j in c0[nlat*n + j].
 template <typename T>
 __global__ void __launch_bounds__(MASS_THREADS) mass_partial_kernel(const T *__restrict__ u,
+                                                                    const T *__restrict__ ulo,
                                                                     const double *__restrict__ c0, int nlon,
                                                                     int nlat, int n, double href, double half_dd,
                                                                     double dlam, size_t chunk,
@@ -600,7 +655,11 @@ __global__ void __launch_bounds__(MASS_THREADS) mass_partial_kernel(const T *__r
         const int j = (int)(e / nlon);
         const T *ue = u + e * per;
         double m = 0.0;
-        for (int b = 0; b < n; ++b) m += c0[j * n + b] * (double)ue[b * n];
+        for (int b = 0; b < n; ++b) {
+            double hb = (double)ue[b * n];
+            if (ulo) hb += (double)ulo[e * per + b * n];
+            m += c0[j * n + b] * hb;
+        }
         acc = csum_add(acc, half_dd * m + href * dlam * c0[nlat * n + j]);
     }
     red[threadIdx.x] = acc;
@@ -704,35 +763,38 @@ int dg_launch_stage<DG_REAL>(int n, const StageArgs<DG_REAL> &a, void *stream)
 }
 
 template <>
-int dg_launch_to_internal<DG_REAL>(const double *src, DG_REAL *dst, size_t nel, int nphi, double href, void *stream)
+int dg_launch_to_internal<DG_REAL>(const double *src, DG_REAL *dst, DG_REAL *lo, size_t nel, int nphi, double href,
+                                   void *stream)
 {
     const size_t nval = nel * 3 * nphi;
     const int threads = 256;
     const size_t blocks = (nval + threads - 1) / threads;
     dgk::to_internal_kernel<DG_REAL><<<(unsigned)(blocks < 65535 * 16 ? blocks : 65535 * 16), threads, 0,
-                                       static_cast<cudaStream_t>(stream)>>>(src, dst, nval, 3 * nphi, nphi, href);
+                                       static_cast<cudaStream_t>(stream)>>>(src, dst, lo, nval, 3 * nphi, href);
     return cudaPeekAtLastError() == cudaSuccess ? 0 : 1;
 }
 
 template <>
-int dg_launch_to_api<DG_REAL>(const DG_REAL *src, double *dst, size_t nel, int nphi, double href, void *stream)
+int dg_launch_to_api<DG_REAL>(const DG_REAL *src, const DG_REAL *lo, double *dst, size_t nel, int nphi, double href,
+                              void *stream)
 {
     const size_t nval = nel * 3 * nphi;
     const int threads = 256;
     const size_t blocks = (nval + threads - 1) / threads;
     dgk::to_api_kernel<DG_REAL><<<(unsigned)(blocks < 65535 * 16 ? blocks : 65535 * 16), threads, 0,
-                                  static_cast<cudaStream_t>(stream)>>>(src, dst, nval, 3 * nphi, href);
+                                  static_cast<cudaStream_t>(stream)>>>(src, lo, dst, nval, 3 * nphi, href);
     return cudaPeekAtLastError() == cudaSuccess ? 0 : 1;
 }
 
 template <>
-int dg_launch_mass<DG_REAL>(const DG_REAL *u, const double *c0, int nlon, int nlat, int n, double href, double dlam,
-                            double dth, double scale, double *partials, int nblocks, double *result, void *stream)
+int dg_launch_mass<DG_REAL>(const DG_REAL *u, const DG_REAL *lo, const double *c0, int nlon, int nlat, int n,
+                            double href, double dlam, double dth, double scale, double *partials, int nblocks,
+                            double *result, void *stream)
 {
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const size_t nel = (size_t)nlon * nlat;
     const size_t chunk = (nel + nblocks - 1) / nblocks;
-    dgk::mass_partial_kernel<DG_REAL><<<nblocks, dgk::MASS_THREADS, 0, s>>>(u, c0, nlon, nlat, n, href,
+    dgk::mass_partial_kernel<DG_REAL><<<nblocks, dgk::MASS_THREADS, 0, s>>>(u, lo, c0, nlon, nlat, n, href,
                                                                             0.5 * dlam * dth, dlam, chunk, partials);
     dgk::mass_final_kernel<<<1, dgk::MASS_THREADS, 0, s>>>(partials, nblocks, scale, result);
     return cudaPeekAtLastError() == cudaSuccess ? 0 : 1;
