@@ -163,6 +163,28 @@ dg_status dg_project_nodal(dg_handle h, const double *nodal, size_t len_nodal, d
 dg_status dg_get_time(dg_handle h, double *t);
 dg_status dg_set_time(dg_handle h, double t);
 
+/* The paper has no counterpart to this entry point.
+ * The time step of dg_max_dt for an FP64 state that the caller already holds
+ * in device memory (layout as above, full depth h), for callers that cannot
+ * allocate device memory and therefore cannot create a handle: code that runs
+ * while a CUDA graph is being captured (cudaMalloc is not permitted there), or
+ * an application whose own memory manager owns the device and forbids other
+ * cudaMalloc calls.  It allocates nothing: its only scratch is one fixed array
+ * of DG_NOALLOC_MAX_NLAT + 1 64-bit words (64 KiB) inside the library, which
+ * every GPU that loads the library holds until the process exits.  Meshes with
+ * more than DG_NOALLOC_MAX_NLAT latitude rows are rejected with DG_EINVAL.
+ * The result, dt = cfl H / (max(p,1) c) as for dg_max_dt, or -1 if h <= 0 or
+ * NaN at a Gauss point, is written to the device double *d_dt; the work is
+ * enqueued on `stream` (a cudaStream_t, NULL = the default stream) and the
+ * call returns without waiting.  The first call on a device sets that device
+ * up (finds the scratch array's device address and copies a small basis table
+ * to constant memory), so make it before any stream capture begins.  All calls
+ * share the one scratch array and each call overwrites it: calls whose work
+ * overlaps on the GPU (unordered streams) race and can return wrong values. */
+#define DG_NOALLOC_MAX_NLAT 8192
+dg_status dg_max_dt_noalloc(const double *d_modal, int nlon, int nlat, int degree, double radius, double g,
+                            double cfl, double *d_dt, void *stream);
+
 /* Number of fused stage-kernel launches issued by this handle so far. */
 long long dg_stage_launches(dg_handle h);
 

@@ -826,6 +826,8 @@ dg_status dg_set_time(dg_handle h, double t)
 
 }  // extern "C"
 
+void dg_set_last_error(const char *msg) { g_err = msg ? msg : ""; }
+
 int dg_mass_blocks(size_t nel)
 {
     size_t b = (nel + 1023) / 1024;

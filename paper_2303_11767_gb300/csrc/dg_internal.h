@@ -108,3 +108,6 @@ template <typename T>
 int dg_launch_max_speed(const T *u, int nlon, int nlat, int n, double href, double g,
                         unsigned long long *maxbits, unsigned int *status, void *stream);
 int dg_mass_blocks(size_t nel);
+
+// dg_api.cpp: set the calling thread's message returned by dg_last_error().
+void dg_set_last_error(const char *msg);

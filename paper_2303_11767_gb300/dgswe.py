@@ -49,6 +49,8 @@ SIGNATURES = {
     "dg_get_time": (ctypes.c_int, [_H, _dp]),
     "dg_set_time": (ctypes.c_int, [_H, ctypes.c_double]),
     "dg_stage_launches": (ctypes.c_longlong, [_H]),
+    "dg_max_dt_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                         ctypes.c_double, ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p]),
     "dg_last_error": (ctypes.c_char_p, [_H]),
 }
 
