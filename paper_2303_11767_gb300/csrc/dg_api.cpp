@@ -266,9 +266,13 @@ dg_status upload_rows(dg_ctx *h, RowTab<T> **dst)
             d.cosn[a] = (T)s.cosn[a];
             d.sinn[a] = (T)s.sinn[a];
             d.rho[a] = (T)s.rho[a];
+            d.CSE[a] = (T)s.CSE[a];
+            d.CSW[a] = (T)s.CSW[a];
             for (int b = 0; b < DG_MAXN; ++b) {
                 d.Ci[a][b] = (T)s.Ci[a][b];
                 d.Q[a][b] = (T)s.Q[a][b];
+                d.QT[a][b] = (T)s.QT[a][b];
+                d.PT[a][b] = (T)s.PT[a][b];
             }
         }
         d.ce_s = (T)s.ce_s;

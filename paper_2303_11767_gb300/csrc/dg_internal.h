@@ -24,6 +24,9 @@ struct BasisTab {
 //   ce_s/ce_n: cos(theta) at the south / north edge (0 at a pole edge)
 //   Ci:  inverse of C_j[b][b'] = int L_b L_b' cos(theta(eta)) deta
 //   Q:   Ci * WLV, i.e. Q[b][q] = sum_b' Ci[b][b'] w_q L_b'(eta_q)
+//   QT, PT: the transposes [q][b] of Q and of Ci * WLD (the beta-pass with
+//        the inverse mass matrix folded in, read one Gauss point at a time)
+//   CSE, CSW: Ci * L(+1), Ci * L(-1) (north / south lift)
 //   rho: hv tendency of the (a = 0, b) modes produced by a unit constant
 //        pressure flux (the rest state with g h^2 / 2 = 1), n-point rules
 template <typename T>
@@ -33,6 +36,10 @@ struct RowTab {
     T ce_s, ce_n;
     T Ci[DG_MAXN][DG_MAXN];
     T Q[DG_MAXN][DG_MAXN];
+    T QT[DG_MAXN][DG_MAXN];
+    T PT[DG_MAXN][DG_MAXN];
+    T CSE[DG_MAXN];
+    T CSW[DG_MAXN];
     T rho[DG_MAXN];
 };
 

@@ -36,6 +36,24 @@ __constant__ BasisTab<DG_REAL> c_basis[DG_MAXN];
 
 namespace dgk {
 
+// Smallest slot stride S >= base for which lanes (g, k), g < G, k < N, that
+// access word g*S + k of a slotted array hit 32 different banks.
+constexpr int bank_free_stride(int base, int N, int G)
+{
+    for (int S = base; S < base + 64; ++S) {
+        bool used[32] = {};
+        bool ok = true;
+        for (int g = 0; g < G && ok; ++g)
+            for (int k = 0; k < N && ok; ++k) {
+                const int b = (g * S + k) % 32;
+                if (used[b]) ok = false;
+                used[b] = true;
+            }
+        if (ok) return S;
+    }
+    return base;
+}
+
 template <int N>
 struct Geo {
     static constexpr int G = 32 / N;            // elements per warp
@@ -45,19 +63,34 @@ struct Geo {
     static constexpr int T1_OFF = 0;            // [f][alpha][SA]
     static constexpr int EW_OFF = 3 * N * SA;   // [f][2][N]
     static constexpr int X_OFF = 0;             // [f][2][alpha][SA]   (reuses T1/EW)
-    static constexpr int FS_OFF = 6 * N * SA;   // [f][2][N]
-    static constexpr int WB_MIN = 6 * N * SA + 6 * N;
+    static constexpr int WB_MIN = 6 * N * SA;
     // element stride in the warp buffer, padded to spread groups over banks
     static constexpr int WB = WB_MIN + ((N - (WB_MIN % 32)) % 32 + 32) % 32;
     static constexpr int TW = G + 2;            // padded tile width (halo columns)
     static constexpr int TH = DG_WARPS + 2;     // padded tile height (halo rows)
-    static constexpr int TRC = 4 * 3 * N;       // trace values per slot
+    // slot strides padded so that the N lanes of the G elements of a warp
+    // touch distinct banks
+    static constexpr int TRC = bank_free_stride(12 * N, N, 32 / N);   // traces W,E,S,N x 3 x N
+    static constexpr int EFC = bank_free_stride(6 * N, N, 32 / N);    // edge fluxes W,S x 3 x N
     static constexpr int HALO_MAX = 2 * DG_WARPS * N + 2 * G * N;
     static_assert(HALO_MAX <= 32 * DG_WARPS, "halo items exceed the block");
 };
 
 template <typename T>
-__device__ __forceinline__ T rcp(T x) { return T(1) / x; }
+__device__ __forceinline__ T rcp(T x);
+template <>
+__device__ __forceinline__ double rcp<double>(double x) { return 1.0 / x; }
+// FP32: the SFU reciprocal (<= 2 ulp), far inside the FP32 tolerance
+template <>
+__device__ __forceinline__ float rcp<float>(float x) { return __fdividef(1.0f, x); }
+
+template <typename T>
+__device__ __forceinline__ T wave_sqrt(T x);
+template <>
+__device__ __forceinline__ double wave_sqrt<double>(double x) { return sqrt(x); }
+// FP32: x * rsqrt(x) on the SFU; only feeds the Rusanov dissipation speed
+template <>
+__device__ __forceinline__ float wave_sqrt<float>(float x) { return x * rsqrtf(x); }
 
 // h <= 0 makes u = hu/h meaningless; a NaN depth is reported as non-finite.
 template <typename T>
@@ -79,7 +112,7 @@ __device__ __forceinline__ void lam_flux(const T *q, T href, T g, T *f, T &speed
     f[0] = q[1];
     f[1] = q[1] * u + P;
     f[2] = q[2] * u;
-    speed = fabs(u) + sqrt(g * h);
+    speed = fabs(u) + wave_sqrt(g * h);
 }
 
 template <typename T>
@@ -92,7 +125,7 @@ __device__ __forceinline__ void th_flux(const T *q, T href, T g, T *f, T &speed,
     f[0] = q[2];
     f[1] = q[1] * v;
     f[2] = q[2] * v + P;
-    speed = fabs(v) + sqrt(g * h);
+    speed = fabs(v) + wave_sqrt(g * h);
 }
 
 // Rusanov flux through a lambda-face, left state L (west), right state R
@@ -209,12 +242,13 @@ __global__ void __launch_bounds__(32 * DG_WARPS) stage_kernel(const StageArgs<T>
 {
     using GE = Geo<N>;
     constexpr int G = GE::G, NP = GE::NP, EL = GE::EL, SA = GE::SA, WB = GE::WB;
-    constexpr int TW = GE::TW, TRC = GE::TRC;
+    constexpr int TW = GE::TW, TRC = GE::TRC, EFC = GE::EFC;
     const BasisTab<T> &B = c_basis[N - 1];
 
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *wbuf = reinterpret_cast<T *>(smem_raw);
-    T *trc = wbuf + DG_WARPS * G * WB;
+    T *trc = wbuf + DG_WARPS * G * WB;       // [slot][W,E,S,N][f][N] traces
+    T *ef = trc + TW * GE::TH * TRC;         // [slot][W,S][f][N] edge fluxes
 
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
@@ -226,12 +260,15 @@ __global__ void __launch_bounds__(32 * DG_WARPS) stage_kernel(const StageArgs<T>
     const int i = i0 + g, j = j0 + warp;
     const bool valid = lane_ok && g < Gv && warp < Wv;
     const size_t e = valid ? (size_t)j * A.nlon + i : 0;
+    const int own = (warp + 1) * TW + (lane_ok ? g + 1 : 1);   // own slot of the padded tile
     const T href = A.href, gg = A.g;
     unsigned st = 0;
 
     T *wb = wbuf + (warp * G + (lane_ok ? g : 0)) * WB;
 
-    // ---- S0: own modal row b = k of the three fields
+    const RowTab<T> *RT = A.rows + (valid ? j : 0);
+
+    // ---- S0: own modal row b = k of the stage state
     T uh[3][N];
 #pragma unroll
     for (int f = 0; f < 3; ++f) {
@@ -239,6 +276,17 @@ __global__ void __launch_bounds__(32 * DG_WARPS) stage_kernel(const StageArgs<T>
         else {
 #pragma unroll
             for (int a = 0; a < N; ++a) uh[f][a] = T(0);
+        }
+    }
+
+    // rows the epilogue will read: start moving them towards L1 now
+    if (valid) {
+#pragma unroll
+        for (int f = 0; f < 3; ++f) {
+            const size_t off = e * EL + f * NP + k * N;
+            if (A.out_base) asm volatile("prefetch.global.L1 [%0];" ::"l"(A.base + off));
+            if (A.lo) asm volatile("prefetch.global.L1 [%0];" ::"l"(A.lo + off));
+            if (A.acc_in) asm volatile("prefetch.global.L1 [%0];" ::"l"(A.acc_in + off));
         }
     }
 
@@ -301,7 +349,7 @@ __global__ void __launch_bounds__(32 * DG_WARPS) stage_kernel(const StageArgs<T>
         }
     }
     if (valid) {
-        T *slot = trc + ((warp + 1) * TW + (g + 1)) * TRC;
+        T *slot = trc + own * TRC;
 #pragma unroll
         for (int s = 0; s < 4; ++s)
 #pragma unroll
@@ -313,7 +361,7 @@ __global__ void __launch_bounds__(32 * DG_WARPS) stage_kernel(const StageArgs<T>
         const int nWE = Wv * N;
         const bool hasS = j0 > 0, hasN = j0 + Wv < A.nlat;
         const int nS = hasS ? Gv * N : 0, nN = hasN ? Gv * N : 0;
-        int it = tid;
+        const int it = tid;   // whole warps take halo items (no divergence inside a warp)
         if (it < 2 * nWE + nS + nN) {
             int he_i, he_j, side, kk, sl;
             if (it < 2 * nWE) {                 // west / east halo columns
@@ -368,47 +416,79 @@ __global__ void __launch_bounds__(32 * DG_WARPS) stage_kernel(const StageArgs<T>
     }
     __syncthreads();
 
-    // ---- S5 Rusanov fluxes at own edge points (W, E at eta_k; S, N at xi_k)
-    const RowTab<T> *RT = A.rows + (valid ? j : 0);
-    T FsW[3], FsE[3], GsS[3], GsN[3];
+    // ---- S5 Rusanov fluxes, each edge once: every element evaluates its W
+    //      edge (at eta_k) and S edge (at xi_k); the tile's east column and top
+    //      row borrow the W / S edges of the east and north halo slots
     {
-        const T *own = trc + ((warp + 1) * TW + (g + 1)) * TRC;
-        const T *sW = own - TRC, *sE = own + TRC;
-        const T *sS = own - TW * TRC, *sN = own + TW * TRC;
-        T nb[3];
+        T nb[3], fx[3];
+        if (valid) {
+            const T *tW = trc + (own - 1) * TRC;
 #pragma unroll
-        for (int f = 0; f < 3; ++f) nb[f] = valid ? sW[(1 * 3 + f) * N + k] : tr[0][f];
-        rusanov_lam(nb, tr[0], href, gg, A.cF, FsW, st);
+            for (int f = 0; f < 3; ++f) nb[f] = tW[(1 * 3 + f) * N + k];       // W neighbour's E trace
+            rusanov_lam(nb, tr[0], href, gg, A.cF, fx, st);
 #pragma unroll
-        for (int f = 0; f < 3; ++f) nb[f] = valid ? sE[(0 * 3 + f) * N + k] : tr[1][f];
-        rusanov_lam(tr[1], nb, href, gg, A.cF, FsE, st);
-        const T ces = __ldg(&RT->ce_s), cen = __ldg(&RT->ce_n);
-        if (valid && j > 0) {
+            for (int f = 0; f < 3; ++f) ef[(own * 2 + 0) * 3 * N + f * N + k] = fx[f];
+            if (j > 0) {
+                const T *tS = trc + (own - TW) * TRC;
 #pragma unroll
-            for (int f = 0; f < 3; ++f) nb[f] = sS[(3 * 3 + f) * N + k];
-            rusanov_th(nb, tr[2], href, gg, A.cG * ces, GsS, st);
-        } else {
+                for (int f = 0; f < 3; ++f) nb[f] = tS[(3 * 3 + f) * N + k];   // S neighbour's N trace
+                rusanov_th(nb, tr[2], href, gg, A.cG * __ldg(&RT->ce_s), fx, st);
+            } else {
 #pragma unroll
-            for (int f = 0; f < 3; ++f) GsS[f] = T(0);   // pole edge: zero flux
+                for (int f = 0; f < 3; ++f) fx[f] = T(0);                       // pole edge: zero flux
+            }
+#pragma unroll
+            for (int f = 0; f < 3; ++f) ef[(own * 2 + 1) * 3 * N + f * N + k] = fx[f];
         }
-        if (valid && j < A.nlat - 1) {
+        const int nE = Wv * N, nN = (j0 + Wv < A.nlat) ? Gv * N : 0;
+        const int it = 32 * DG_WARPS - 1 - tid;   // the last warps, which have no halo items
+        if (it < nE + nN) {
+            T L[3], R[3];
+            if (it < nE) {                      // E edge of the last valid column
+                const int w = it / N, kk = it - (it / N) * N;
+                const int sl = (w + 1) * TW + Gv, sr = sl + 1;
 #pragma unroll
-            for (int f = 0; f < 3; ++f) nb[f] = sN[(2 * 3 + f) * N + k];
-            rusanov_th(tr[3], nb, href, gg, A.cG * cen, GsN, st);
-        } else {
+                for (int f = 0; f < 3; ++f) {
+                    L[f] = trc[sl * TRC + (1 * 3 + f) * N + kk];
+                    R[f] = trc[sr * TRC + (0 * 3 + f) * N + kk];
+                }
+                rusanov_lam(L, R, href, gg, A.cF, fx, st);
 #pragma unroll
-            for (int f = 0; f < 3; ++f) GsN[f] = T(0);   // pole edge: zero flux
+                for (int f = 0; f < 3; ++f) ef[(sr * 2 + 0) * 3 * N + f * N + kk] = fx[f];
+            } else {                            // N edge of the top valid row
+                const int r = it - nE, c = r / N, kk = r - (r / N) * N;
+                const int sl = Wv * TW + c + 1, su = sl + TW;
+#pragma unroll
+                for (int f = 0; f < 3; ++f) {
+                    L[f] = trc[sl * TRC + (3 * 3 + f) * N + kk];
+                    R[f] = trc[su * TRC + (2 * 3 + f) * N + kk];
+                }
+                rusanov_th(L, R, href, gg, A.cG * __ldg(&A.rows[j0 + Wv - 1].ce_n), fx, st);
+#pragma unroll
+                for (int f = 0; f < 3; ++f) ef[(su * 2 + 1) * 3 * N + f * N + kk] = fx[f];
+            }
         }
     }
+    __syncthreads();
 
-    // ---- S2 pointwise fluxes at (alpha = k, beta) and S3 beta-pass, with the
-    //      N/S lift folded in and the inverse mass matrix applied along b
+    // ---- S2 pointwise fluxes at (alpha = k, beta), S3 beta-pass with the
+    //      inverse mass matrix folded in (per-row QT = (Ci W L)^T, PT = (Ci W L')^T)
+    //      and the N/S lift through Ci L(+-1)
     {
+        T GsS[3], GsN[3];
+#pragma unroll
+        for (int f = 0; f < 3; ++f) {
+            GsS[f] = ef[(own * 2 + 1) * 3 * N + f * N + k];
+            GsN[f] = (valid && j < A.nlat - 1) ? ef[((own + TW) * 2 + 1) * 3 * N + f * N + k] : T(0);
+        }
         T X1[3][N], X2[3][N];
 #pragma unroll
         for (int f = 0; f < 3; ++f)
 #pragma unroll
-            for (int b = 0; b < N; ++b) { X1[f][b] = T(0); X2[f][b] = T(0); }
+            for (int b = 0; b < N; ++b) {
+                X2[f][b] = __ldg(&RT->CSW[b]) * GsS[f] - __ldg(&RT->CSE[b]) * GsN[f];
+                X1[f][b] = T(0);
+            }
 #pragma unroll
         for (int q = 0; q < N; ++q) {
             const T hp = qn[0][q], hu = qn[1][q], hv = qn[2][q];
@@ -425,7 +505,7 @@ __global__ void __launch_bounds__(32 * DG_WARPS) stage_kernel(const StageArgs<T>
             const T S1 = K * hv, S2 = -(P * s * A.invR) - K * hu;
 #pragma unroll
             for (int b = 0; b < N; ++b) {
-                const T wl = B.WLV[b][q], wd = B.WLD[b][q];
+                const T wl = __ldg(&RT->QT[q][b]), wd = __ldg(&RT->PT[q][b]);
                 X1[0][b] = fma(wl, F0, X1[0][b]);
                 X1[1][b] = fma(wl, F1, X1[1][b]);
                 X1[2][b] = fma(wl, F2, X1[2][b]);
@@ -434,31 +514,14 @@ __global__ void __launch_bounds__(32 * DG_WARPS) stage_kernel(const StageArgs<T>
                 X2[2][b] = fma(wd, G2, fma(wl, S2, X2[2][b]));
             }
         }
-#pragma unroll
-        for (int f = 0; f < 3; ++f)
-#pragma unroll
-            for (int b = 0; b < N; ++b) X2[f][b] -= B.SE[b] * GsN[f] - B.SW[b] * GsS[f];
-        // S7 inverse mass matrix along b (per row table), then hand over
         if (lane_ok) {
 #pragma unroll
             for (int f = 0; f < 3; ++f)
 #pragma unroll
                 for (int b = 0; b < N; ++b) {
-                    T y1 = T(0), y2 = T(0);
-#pragma unroll
-                    for (int c = 0; c < N; ++c) {
-                        const T ci = __ldg(&RT->Ci[b][c]);
-                        y1 = fma(ci, X1[f][c], y1);
-                        y2 = fma(ci, X2[f][c], y2);
-                    }
-                    wb[GE::X_OFF + ((f * 2 + 0) * N + k) * SA + b] = y1;
-                    wb[GE::X_OFF + ((f * 2 + 1) * N + k) * SA + b] = y2;
+                    wb[GE::X_OFF + ((f * 2 + 0) * N + k) * SA + b] = X1[f][b];
+                    wb[GE::X_OFF + ((f * 2 + 1) * N + k) * SA + b] = X2[f][b];
                 }
-#pragma unroll
-            for (int f = 0; f < 3; ++f) {
-                wb[GE::FS_OFF + (f * 2 + 0) * N + k] = FsE[f];
-                wb[GE::FS_OFF + (f * 2 + 1) * N + k] = FsW[f];
-            }
         }
     }
     __syncwarp();
@@ -469,6 +532,8 @@ __global__ void __launch_bounds__(32 * DG_WARPS) stage_kernel(const StageArgs<T>
 #pragma unroll
         for (int q = 0; q < N; ++q) Qk[q] = __ldg(&RT->Q[k][q]);
         const T rhok = __ldg(&RT->rho[k]);
+        const T *efW = ef + (own * 2 + 0) * 3 * N;          // W edge fluxes of this element
+        const T *efE = ef + ((own + 1) * 2 + 0) * 3 * N;    // = W edge fluxes of the E neighbour
         T kk[3][N];
 #pragma unroll
         for (int f = 0; f < 3; ++f) {
@@ -478,8 +543,8 @@ __global__ void __launch_bounds__(32 * DG_WARPS) stage_kernel(const StageArgs<T>
             for (int q = 0; q < N; ++q) {
                 y1[q] = wb[GE::X_OFF + ((f * 2 + 0) * N + q) * SA + k];
                 y2[q] = wb[GE::X_OFF + ((f * 2 + 1) * N + q) * SA + k];
-                ye = fma(Qk[q], wb[GE::FS_OFF + (f * 2 + 0) * N + q], ye);
-                yw = fma(Qk[q], wb[GE::FS_OFF + (f * 2 + 1) * N + q], yw);
+                ye = fma(Qk[q], efE[f * N + q], ye);
+                yw = fma(Qk[q], efW[f * N + q], yw);
             }
 #pragma unroll
             for (int a = 0; a < N; ++a) {
@@ -559,7 +624,7 @@ template <typename T, int N>
 size_t stage_smem_bytes()
 {
     using GE = Geo<N>;
-    return sizeof(T) * ((size_t)DG_WARPS * GE::G * GE::WB + (size_t)GE::TW * GE::TH * GE::TRC);
+    return sizeof(T) * ((size_t)DG_WARPS * GE::G * GE::WB + (size_t)GE::TW * GE::TH * (GE::TRC + GE::EFC));
 }
 
 template <typename T, int N>

@@ -163,10 +163,24 @@ int dg_build_tables(HostTables &t, int nlon, int nlat, int p, double R, double g
             for (int c = 0; c < n; ++c) r.Ci[b][c] = Ci[b * n + c];
         for (int b = 0; b < n; ++b)
             for (int q = 0; q < n; ++q) {
-                double s = 0.0;
-                for (int c = 0; c < n; ++c) s += Ci[b * n + c] * t.basis.WLV[c][q];
+                double s = 0.0, sd = 0.0;
+                for (int c = 0; c < n; ++c) {
+                    s += Ci[b * n + c] * t.basis.WLV[c][q];
+                    sd += Ci[b * n + c] * t.basis.WLD[c][q];
+                }
                 r.Q[b][q] = s;
+                r.QT[q][b] = s;
+                r.PT[q][b] = sd;
             }
+        for (int b = 0; b < n; ++b) {
+            double se = 0.0, sw = 0.0;
+            for (int c = 0; c < n; ++c) {
+                se += Ci[b * n + c] * t.basis.SE[c];
+                sw += Ci[b * n + c] * t.basis.SW[c];
+            }
+            r.CSE[b] = se;
+            r.CSW[b] = sw;
+        }
         // Unit pressure flux, fluid at rest: G_hv = cG cos(theta) (scaled flux),
         // S_hv = -sin(theta)/R, edge fluxes cG ce; the column contraction gives
         // x2[b], the row contraction with w L_0 = sqrt(2) w, then Ci.
