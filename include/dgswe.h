@@ -72,8 +72,11 @@ typedef enum {
                                     (returns DG_EUNSUPPORTED) */
     DG_OPT_STREAM = 5,           /* cudaStream_t cast to long long; 0 = the
                                     library's own non-blocking stream */
-    DG_OPT_STEPS_PER_GRAPH = 6   /* time steps captured per CUDA graph, 1..1024,
+    DG_OPT_STEPS_PER_GRAPH = 6,  /* time steps captured per CUDA graph, 1..1024,
                                     default 16 */
+    DG_OPT_TILE_ROWS = 7,        /* ensemble only: latitude rows per CTA tile, 4 or 8
+                                    (default 8; dg_ensemble_autotune picks it) */
+    DG_OPT_BLOCKS_PER_SM = 8     /* ensemble only: persistent CTAs per SM, 1..8 (default 2) */
 } dg_option;
 
 /* Make CUDA device `device` current for the calling thread in this library
@@ -162,6 +165,45 @@ dg_status dg_project_nodal(dg_handle h, const double *nodal, size_t len_nodal, d
 /* Simulated time of the resident state (advanced by dg_step). */
 dg_status dg_get_time(dg_handle h, double *t);
 dg_status dg_set_time(dg_handle h, double t);
+
+/* ------------------------------------------------------------------------
+ * Batched ensemble: many independent meshes of uneven sizes and degrees (the
+ * decoupled copies of the 2-D problem of the paper's vertical-levels
+ * experiment, Sec. 5.2.2), advanced together in FP32 by one persistent
+ * launch per SSP-RK3 stage (Table "Butcher") inside a captured CUDA graph.
+ * Each member has its own state (same layout as above), its own time step
+ * and its own reference depth; members never interact.
+ * ------------------------------------------------------------------------ */
+typedef struct dg_ens *dg_ensemble;
+
+/* members >= 1 meshes; member m has nlon[m] x nlat[m] elements of degree
+ * degree[m] (0..4).  Allocates all state arrays on the current device. */
+dg_status dg_ensemble_create(int members, const int *nlon, const int *nlat, const int *degree, double radius,
+                             double g, double omega, dg_ensemble *out);
+dg_status dg_ensemble_destroy(dg_ensemble e);
+/* DG_OPT_STREAM, DG_OPT_STEPS_PER_GRAPH, DG_OPT_TILE_ROWS, DG_OPT_BLOCKS_PER_SM. */
+dg_status dg_ensemble_set_option(dg_ensemble e, int key, long long value);
+/* Values in member m's state (0 for a bad member index). */
+size_t dg_ensemble_state_len(dg_ensemble e, int member);
+/* Values in one state array of the whole ensemble (the ensemble's DOF). */
+size_t dg_ensemble_total_dof(dg_ensemble e);
+/* Copy member m's modal state in / out (host buffers, layout above). */
+dg_status dg_ensemble_set_state(dg_ensemble e, int member, const double *modal, size_t len);
+dg_status dg_ensemble_get_state(dg_ensemble e, int member, double *modal, size_t len);
+/* One time step per member (dt[m] > 0), used by every following dg_ensemble_step. */
+dg_status dg_ensemble_set_dt(dg_ensemble e, const double *dt, int members);
+/* n SSP-RK3 steps of every member; reports DG_ENONFINITE / DG_ENONPHYSICAL. */
+dg_status dg_ensemble_step(dg_ensemble e, int n);
+/* Total mass and CFL time step of member m, as dg_total_mass / dg_max_dt. */
+dg_status dg_ensemble_total_mass(dg_ensemble e, int member, double *mass);
+dg_status dg_ensemble_max_dt(dg_ensemble e, int member, double cfl, double *dt);
+/* Autotuner: times `trials` steps for every tile height (4, 8 rows per CTA)
+ * and persistent grid size (1..4 CTAs per SM) on the ensemble's own state
+ * (saved and restored), keeps the fastest and returns it, with the time of
+ * one step in ms. */
+dg_status dg_ensemble_autotune(dg_ensemble e, int trials, int *tile_rows, int *blocks_per_sm, double *best_ms);
+/* Persistent stage launches issued so far (one per RK stage). */
+long long dg_ensemble_stage_launches(dg_ensemble e);
 
 /* The paper has no counterpart to this entry point.
  * The time step of dg_max_dt for an FP64 state that the caller already holds

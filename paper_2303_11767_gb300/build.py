@@ -16,7 +16,8 @@ NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I" + os.path.join(HERE, "..", "include")]
-SOURCES = ["dg_kernels_f32.cu", "dg_kernels_f64.cu", "dg_api.cpp", "dg_tables.cpp", "dg_noalloc.cu"]
+SOURCES = ["dg_kernels_f32.cu", "dg_kernels_f64.cu", "dg_api.cpp", "dg_tables.cpp", "dg_noalloc.cu",
+           "dg_ensemble.cpp"]
 
 
 def _deps():

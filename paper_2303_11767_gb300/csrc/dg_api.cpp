@@ -832,6 +832,8 @@ dg_status dg_set_time(dg_handle h, double t)
 
 void dg_set_last_error(const char *msg) { g_err = msg ? msg : ""; }
 
+int dg_ensure_basis(int device) { return upload_basis_once(device) == DG_OK ? 0 : 1; }
+
 int dg_mass_blocks(size_t nel)
 {
     size_t b = (nel + 1023) / 1024;

@@ -91,6 +91,41 @@ struct StageArgs {
     T ci, ca, cc, cd, dt;
 };
 
+// Batched ensemble: the members' states are concatenated in every state
+// array; one persistent launch per stage walks a work list of tiles.
+template <typename T>
+struct EnsMember {
+    long long off;   // offset of the member's first value in the state arrays
+    int rows;        // index of the member's first row table
+    int nlon, nlat, n;
+    T href, P0, cF, cG, dt;
+};
+
+struct EnsItem {
+    int member, tx, ty, cost;
+};
+
+template <typename T>
+struct EnsArgs {
+    const T *base, *inc, *lo, *acc_in;
+    T *out_rhs, *inc_out, *acc_out, *out_base, *out_lo;
+    const RowTab<T> *rows;
+    const EnsMember<T> *members;
+    const EnsItem *items;
+    int nitems;
+    unsigned int *status;
+    T g, invR, twoOmega;
+    T ci, ca, cc, cd;
+};
+
+// tile rows (warps per CTA) the ensemble kernel is built for
+#define DG_ENS_TILE_ROWS_A 4
+#define DG_ENS_TILE_ROWS_B 8
+
+template <typename T>
+int dg_launch_ensemble_stage(int tile_rows, int grid, const EnsArgs<T> &a, void *stream);
+int dg_ensemble_tile_width(int n);   // elements per warp for degree n - 1
+
 // status bits written by device code
 #define DG_STATUS_NONPHYSICAL 1u
 #define DG_STATUS_NONFINITE 2u
@@ -118,3 +153,6 @@ int dg_mass_blocks(size_t nel);
 
 // dg_api.cpp: set the calling thread's message returned by dg_last_error().
 void dg_set_last_error(const char *msg);
+// dg_api.cpp: make sure the constant basis tables are on device `device`
+// (0 on success).
+int dg_ensure_basis(int device);

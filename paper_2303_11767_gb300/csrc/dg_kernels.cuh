@@ -54,7 +54,7 @@ constexpr int bank_free_stride(int base, int N, int G)
     return base;
 }
 
-template <int N>
+template <int N, int W>
 struct Geo {
     static constexpr int G = 32 / N;            // elements per warp
     static constexpr int NP = N * N;            // modes per field
@@ -67,13 +67,14 @@ struct Geo {
     // element stride in the warp buffer, padded to spread groups over banks
     static constexpr int WB = WB_MIN + ((N - (WB_MIN % 32)) % 32 + 32) % 32;
     static constexpr int TW = G + 2;            // padded tile width (halo columns)
-    static constexpr int TH = DG_WARPS + 2;     // padded tile height (halo rows)
+    static constexpr int TH = W + 2;            // padded tile height (halo rows)
     // slot strides padded so that the N lanes of the G elements of a warp
     // touch distinct banks
     static constexpr int TRC = bank_free_stride(12 * N, N, 32 / N);   // traces W,E,S,N x 3 x N
     static constexpr int EFC = bank_free_stride(6 * N, N, 32 / N);    // edge fluxes W,S x 3 x N
-    static constexpr int HALO_MAX = 2 * DG_WARPS * N + 2 * G * N;
-    static_assert(HALO_MAX <= 32 * DG_WARPS, "halo items exceed the block");
+    static constexpr int HALO_MAX = 2 * W * N + 2 * G * N;
+    static_assert(HALO_MAX <= 32 * W, "halo items exceed the block");
+    static_assert(W * N + G * N <= 32 * W, "boundary flux items exceed the block");
 };
 
 template <typename T>
@@ -237,26 +238,26 @@ __device__ __forceinline__ void load_stage_row(const T *__restrict__ base, const
     }
 }
 
-template <typename T, int N>
-__global__ void __launch_bounds__(32 * DG_WARPS) stage_kernel(const StageArgs<T> A)
+// One tile of G x W elements (tile column bx, tile row by) of one mesh.
+template <typename T, int N, int W>
+__device__ __forceinline__ void stage_tile(const StageArgs<T> &A, int bx, int by, unsigned char *smem_raw)
 {
-    using GE = Geo<N>;
+    using GE = Geo<N, W>;
     constexpr int G = GE::G, NP = GE::NP, EL = GE::EL, SA = GE::SA, WB = GE::WB;
     constexpr int TW = GE::TW, TRC = GE::TRC, EFC = GE::EFC;
     const BasisTab<T> &B = c_basis[N - 1];
 
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     T *wbuf = reinterpret_cast<T *>(smem_raw);
-    T *trc = wbuf + DG_WARPS * G * WB;       // [slot][W,E,S,N][f][N] traces
+    T *trc = wbuf + W * G * WB;              // [slot][W,E,S,N][f][N] traces
     T *ef = trc + TW * GE::TH * TRC;         // [slot][W,S][f][N] edge fluxes
 
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
     const int g = lane / N, k = lane - (lane / N) * N;
     const bool lane_ok = g < G;
-    const int i0 = blockIdx.x * G, j0 = blockIdx.y * DG_WARPS;
+    const int i0 = bx * G, j0 = by * W;
     const int Gv = min(G, A.nlon - i0);
-    const int Wv = min(DG_WARPS, A.nlat - j0);
+    const int Wv = min(W, A.nlat - j0);
     const int i = i0 + g, j = j0 + warp;
     const bool valid = lane_ok && g < Gv && warp < Wv;
     const size_t e = valid ? (size_t)j * A.nlon + i : 0;
@@ -441,7 +442,7 @@ __global__ void __launch_bounds__(32 * DG_WARPS) stage_kernel(const StageArgs<T>
             for (int f = 0; f < 3; ++f) ef[(own * 2 + 1) * 3 * N + f * N + k] = fx[f];
         }
         const int nE = Wv * N, nN = (j0 + Wv < A.nlat) ? Gv * N : 0;
-        const int it = 32 * DG_WARPS - 1 - tid;   // the last warps, which have no halo items
+        const int it = 32 * W - 1 - tid;   // the last warps, which have no halo items
         if (it < nE + nN) {
             T L[3], R[3];
             if (it < nE) {                      // E edge of the last valid column
@@ -620,30 +621,116 @@ __global__ void __launch_bounds__(32 * DG_WARPS) stage_kernel(const StageArgs<T>
     if (st && valid) atomicOr(A.status, st);
 }
 
-template <typename T, int N>
-size_t stage_smem_bytes()
+template <typename T, int N, int W>
+__global__ void __launch_bounds__(32 * W) stage_kernel(const StageArgs<T> A)
 {
-    using GE = Geo<N>;
-    return sizeof(T) * ((size_t)DG_WARPS * GE::G * GE::WB + (size_t)GE::TW * GE::TH * (GE::TRC + GE::EFC));
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    stage_tile<T, N, W>(A, blockIdx.x, blockIdx.y, smem_raw);
+}
+
+template <typename T, int N, int W>
+constexpr size_t stage_smem_bytes()
+{
+    using GE = Geo<N, W>;
+    return sizeof(T) * ((size_t)W * GE::G * GE::WB + (size_t)GE::TW * GE::TH * (GE::TRC + GE::EFC));
 }
 
 template <typename T, int N>
 int launch_stage_n(const StageArgs<T> &a, cudaStream_t s)
 {
-    using GE = Geo<N>;
-    const size_t smem = stage_smem_bytes<T, N>();
+    constexpr int W = DG_WARPS;
+    using GE = Geo<N, W>;
+    const size_t smem = stage_smem_bytes<T, N, W>();
     // the shared-memory opt-in is a per-device function attribute
     static unsigned long long attr_set = 0;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 1;
     if (!(attr_set >> dev & 1ull)) {
-        if (cudaFuncSetAttribute(stage_kernel<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        if (cudaFuncSetAttribute(stage_kernel<T, N, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
             cudaSuccess)
             return 1;
         attr_set |= 1ull << dev;
     }
-    dim3 grid((a.nlon + GE::G - 1) / GE::G, (a.nlat + DG_WARPS - 1) / DG_WARPS);
-    stage_kernel<T, N><<<grid, 32 * DG_WARPS, smem, s>>>(a);
+    dim3 grid((a.nlon + GE::G - 1) / GE::G, (a.nlat + W - 1) / W);
+    stage_kernel<T, N, W><<<grid, 32 * W, smem, s>>>(a);
+    return cudaPeekAtLastError() == cudaSuccess ? 0 : 1;
+}
+
+// ---------------------------------------------------------------- ensemble --
+
+// One persistent launch per RK stage for a batch of meshes of different sizes
+// and degrees: every CTA walks the work list (member, tile column, tile row)
+// and runs the tile with the member's degree.  Items are ordered by cost,
+// largest first, so the round-robin walk balances the CTAs.
+template <typename T, int W>
+__global__ void __launch_bounds__(32 * W, 24 / W) ensemble_kernel(const EnsArgs<T> E)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    for (int it = blockIdx.x; it < E.nitems; it += gridDim.x) {
+        const EnsItem item = E.items[it];
+        const EnsMember<T> m = E.members[item.member];
+        StageArgs<T> A;
+        A.base = E.base + m.off;
+        A.inc = E.inc ? E.inc + m.off : nullptr;
+        A.lo = E.lo ? E.lo + m.off : nullptr;
+        A.acc_in = E.acc_in ? E.acc_in + m.off : nullptr;
+        A.out_rhs = E.out_rhs ? E.out_rhs + m.off : nullptr;
+        A.inc_out = E.inc_out ? E.inc_out + m.off : nullptr;
+        A.acc_out = E.acc_out ? E.acc_out + m.off : nullptr;
+        A.out_base = E.out_base ? E.out_base + m.off : nullptr;
+        A.out_lo = E.out_lo ? E.out_lo + m.off : nullptr;
+        A.rows = E.rows + m.rows;
+        A.status = E.status;
+        A.nlon = m.nlon;
+        A.nlat = m.nlat;
+        A.href = m.href;
+        A.P0 = m.P0;
+        A.g = E.g;
+        A.cF = m.cF;
+        A.cG = m.cG;
+        A.invR = E.invR;
+        A.twoOmega = E.twoOmega;
+        A.ci = E.ci;
+        A.ca = E.ca;
+        A.cc = E.cc;
+        A.cd = E.cd;
+        A.dt = m.dt;
+        switch (m.n) {
+        case 1: stage_tile<T, 1, W>(A, item.tx, item.ty, smem_raw); break;
+        case 2: stage_tile<T, 2, W>(A, item.tx, item.ty, smem_raw); break;
+        case 3: stage_tile<T, 3, W>(A, item.tx, item.ty, smem_raw); break;
+        case 4: stage_tile<T, 4, W>(A, item.tx, item.ty, smem_raw); break;
+        default: stage_tile<T, 5, W>(A, item.tx, item.ty, smem_raw); break;
+        }
+        __syncthreads();   // the next item reuses the shared memory
+    }
+}
+
+template <typename T, int W>
+constexpr size_t ensemble_smem_bytes()
+{
+    size_t m = stage_smem_bytes<T, 1, W>();
+    m = m > stage_smem_bytes<T, 2, W>() ? m : stage_smem_bytes<T, 2, W>();
+    m = m > stage_smem_bytes<T, 3, W>() ? m : stage_smem_bytes<T, 3, W>();
+    m = m > stage_smem_bytes<T, 4, W>() ? m : stage_smem_bytes<T, 4, W>();
+    m = m > stage_smem_bytes<T, 5, W>() ? m : stage_smem_bytes<T, 5, W>();
+    return m;
+}
+
+template <typename T, int W>
+int launch_ensemble_w(int grid, const EnsArgs<T> &a, cudaStream_t s)
+{
+    const size_t smem = ensemble_smem_bytes<T, W>();
+    static unsigned long long attr_set = 0;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 1;
+    if (!(attr_set >> dev & 1ull)) {
+        if (cudaFuncSetAttribute(ensemble_kernel<T, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+            cudaSuccess)
+            return 1;
+        attr_set |= 1ull << dev;
+    }
+    ensemble_kernel<T, W><<<grid, 32 * W, smem, s>>>(a);
     return cudaPeekAtLastError() == cudaSuccess ? 0 : 1;
 }
 
@@ -826,6 +913,17 @@ int dg_launch_stage<DG_REAL>(int n, const StageArgs<DG_REAL> &a, void *stream)
     default: return 1;
     }
 }
+
+#ifdef DG_REAL_IS_F32   // the ensemble runs in FP32 only
+template <>
+int dg_launch_ensemble_stage<DG_REAL>(int tile_rows, int grid, const EnsArgs<DG_REAL> &a, void *stream)
+{
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (tile_rows == DG_ENS_TILE_ROWS_A) return dgk::launch_ensemble_w<DG_REAL, DG_ENS_TILE_ROWS_A>(grid, a, s);
+    if (tile_rows == DG_ENS_TILE_ROWS_B) return dgk::launch_ensemble_w<DG_REAL, DG_ENS_TILE_ROWS_B>(grid, a, s);
+    return 1;
+}
+#endif
 
 template <>
 int dg_launch_to_internal<DG_REAL>(const double *src, DG_REAL *dst, DG_REAL *lo, size_t nel, int nphi, double href,

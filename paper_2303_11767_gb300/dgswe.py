@@ -20,6 +20,7 @@ STATUS_NAMES = {0: "DG_OK", 1: "DG_EINVAL", 2: "DG_ENOMEM", 3: "DG_ECUDA", 4: "D
                 5: "DG_ENONPHYSICAL", 6: "DG_ETIMEOUT", 7: "DG_EUNSUPPORTED"}
 PREC = {"fp64": 0, "fp32": 1, "fp32_tc_bf16": 2, "fp32_tc_fp16": 3}
 OPT_PRECISION, OPT_RK_ORDER, OPT_CHECK_FINITE, OPT_ALPHA_MODE, OPT_STREAM, OPT_STEPS_PER_GRAPH = 1, 2, 3, 4, 5, 6
+OPT_TILE_ROWS, OPT_BLOCKS_PER_SM = 7, 8
 
 EARTH_RADIUS = 6.37122e6
 GRAVITY = 9.80616
@@ -52,6 +53,22 @@ SIGNATURES = {
     "dg_max_dt_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                          ctypes.c_double, ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p]),
     "dg_last_error": (ctypes.c_char_p, [_H]),
+    "dg_ensemble_create": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                          ctypes.POINTER(ctypes.c_int), ctypes.c_double, ctypes.c_double,
+                                          ctypes.c_double, ctypes.POINTER(ctypes.c_void_p)]),
+    "dg_ensemble_destroy": (ctypes.c_int, [_H]),
+    "dg_ensemble_set_option": (ctypes.c_int, [_H, ctypes.c_int, ctypes.c_longlong]),
+    "dg_ensemble_state_len": (ctypes.c_size_t, [_H, ctypes.c_int]),
+    "dg_ensemble_total_dof": (ctypes.c_size_t, [_H]),
+    "dg_ensemble_set_state": (ctypes.c_int, [_H, ctypes.c_int, _dp, ctypes.c_size_t]),
+    "dg_ensemble_get_state": (ctypes.c_int, [_H, ctypes.c_int, _dp, ctypes.c_size_t]),
+    "dg_ensemble_set_dt": (ctypes.c_int, [_H, _dp, ctypes.c_int]),
+    "dg_ensemble_step": (ctypes.c_int, [_H, ctypes.c_int]),
+    "dg_ensemble_total_mass": (ctypes.c_int, [_H, ctypes.c_int, _dp]),
+    "dg_ensemble_max_dt": (ctypes.c_int, [_H, ctypes.c_int, ctypes.c_double, _dp]),
+    "dg_ensemble_autotune": (ctypes.c_int, [_H, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                            ctypes.POINTER(ctypes.c_int), _dp]),
+    "dg_ensemble_stage_launches": (ctypes.c_longlong, [_H]),
 }
 
 _lib = None
@@ -222,3 +239,86 @@ class Solver:
         vals = [np.asarray(v, dtype=np.float64).reshape(self.nlat, nm, self.nlon, nm).transpose(0, 2, 1, 3)
                 for v in fn_grid(lam, th)]
         return self.project_nodal(np.ascontiguousarray(np.stack(vals, axis=2)))
+
+
+class Ensemble:
+    """A batch of independent meshes advanced together (FP32, SSP-RK3); see
+    include/dgswe.h."""
+
+    def __init__(self, nlon, nlat, degree, radius=EARTH_RADIUS, g=GRAVITY, omega=OMEGA):
+        L = lib()
+        nm = len(nlon)
+        self.nlon, self.nlat, self.degree = list(map(int, nlon)), list(map(int, nlat)), list(map(int, degree))
+        arr = ctypes.c_int * nm
+        h = ctypes.c_void_p()
+        _check(L.dg_ensemble_create(nm, arr(*self.nlon), arr(*self.nlat), arr(*self.degree), float(radius),
+                                    float(g), float(omega), ctypes.byref(h)))
+        self._h = h
+        self.members = nm
+        self.radius = float(radius)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().dg_ensemble_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def set_option(self, key, value):
+        _check(lib().dg_ensemble_set_option(self._h, int(key), int(value)), self._h)
+
+    def state_len(self, m):
+        return int(lib().dg_ensemble_state_len(self._h, int(m)))
+
+    def shape(self, m):
+        n = self.degree[m] + 1
+        return (self.nlat[m], self.nlon[m], 3, n * n)
+
+    @property
+    def total_dof(self):
+        return int(lib().dg_ensemble_total_dof(self._h))
+
+    def set_state(self, m, u):
+        u = np.ascontiguousarray(u, dtype=np.float64).reshape(-1)
+        _check(lib().dg_ensemble_set_state(self._h, int(m), _ptr(u), u.size), self._h)
+
+    def get_state(self, m):
+        out = np.empty(self.state_len(m))
+        _check(lib().dg_ensemble_get_state(self._h, int(m), _ptr(out), out.size), self._h)
+        return out.reshape(self.shape(m))
+
+    def set_dt(self, dt):
+        d = np.ascontiguousarray(dt, dtype=np.float64)
+        _check(lib().dg_ensemble_set_dt(self._h, _ptr(d), d.size), self._h)
+
+    def step(self, n):
+        _check(lib().dg_ensemble_step(self._h, int(n)), self._h)
+
+    def total_mass(self, m):
+        x = ctypes.c_double()
+        _check(lib().dg_ensemble_total_mass(self._h, int(m), ctypes.byref(x)), self._h)
+        return x.value
+
+    def max_dt(self, m, cfl):
+        x = ctypes.c_double()
+        _check(lib().dg_ensemble_max_dt(self._h, int(m), float(cfl), ctypes.byref(x)), self._h)
+        return x.value
+
+    def autotune(self, trials=3):
+        w, b, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+        _check(lib().dg_ensemble_autotune(self._h, int(trials), ctypes.byref(w), ctypes.byref(b), ctypes.byref(ms)),
+               self._h)
+        return w.value, b.value, ms.value
+
+    def stage_launches(self):
+        return int(lib().dg_ensemble_stage_launches(self._h))

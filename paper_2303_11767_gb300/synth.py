@@ -187,3 +187,19 @@ CONFIG_SEEDS = {"c1": 1, "c2": 2, "c3": 3}
 
 def ensemble_member_seed(k: int) -> int:
     return 1000 + int(k)
+
+
+def ensemble_members(count: int = 256, seed: int = 4, nlat_range=(20, 180), degrees=(1, 2, 3, 4)):
+    """Mesh sizes of a batched ensemble: nlat uniform on the integers of
+    nlat_range, nlon = 2 nlat, degree uniform on `degrees` (splitmix64 draws).
+    Returns lists (nlon, nlat, degree)."""
+    gen = splitmix64(seed)
+    lo, hi = nlat_range
+    nlon, nlat, deg = [], [], []
+    for _ in range(count):
+        la = lo + next(gen) % (hi - lo + 1)
+        d = degrees[next(gen) % len(degrees)]
+        nlat.append(int(la))
+        nlon.append(int(2 * la))
+        deg.append(int(d))
+    return nlon, nlat, deg
