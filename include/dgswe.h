@@ -167,6 +167,48 @@ dg_status dg_get_time(dg_handle h, double *t);
 dg_status dg_set_time(dg_handle h, double t);
 
 /* ------------------------------------------------------------------------
+ * Learned correction: a per-element multilayer perceptron (n_in -> H -> H ->
+ * n_out, GELU (erf form), BF16 weights, FP32 accumulation, FP32 master
+ * weights and Adam moments) trained on the GPU by the library's own forward
+ * and backward kernels, used as an added modal source term of a degree-1
+ * solver.  The paper has no learned component; this is the ML extension of
+ * the method built on it (trained on pairs the method itself generates).
+ * Batches are row-major FP32 device arrays [batch][features], batch <= 8192.
+ * ------------------------------------------------------------------------ */
+typedef struct dg_mlp_ctx *dg_mlp;
+
+/* He-uniform weights from `seed`, zero biases, identity normalisation. */
+dg_status dg_mlp_create(int n_in, int n_hidden, int n_out, unsigned long long seed, dg_mlp *out);
+dg_status dg_mlp_destroy(dg_mlp m);
+/* Number of parameters; layout W1[H][n_in], b1[H], W2[H][H], b2[H],
+ * W3[n_out][H], b3[n_out]. */
+size_t dg_mlp_num_params(dg_mlp m);
+dg_status dg_mlp_get_params(dg_mlp m, float *params, size_t n);   /* host buffer */
+dg_status dg_mlp_set_params(dg_mlp m, const float *params, size_t n);
+/* Inputs are used as (x - in_mean) / in_std; the network predicts targets as
+ * (t - out_mean) / out_std (host arrays of n_in and n_out values, std > 0). */
+dg_status dg_mlp_set_normalization(dg_mlp m, const float *in_mean, const float *in_std, const float *out_mean,
+                                   const float *out_std);
+/* Normalised network output of a batch (device arrays). */
+dg_status dg_mlp_forward(dg_mlp m, const float *d_x, int batch, float *d_y);
+/* Mean squared error on normalised targets and its gradient (host buffer of
+ * dg_mlp_num_params values, same layout as the parameters). */
+dg_status dg_mlp_gradients(dg_mlp m, const float *d_x, const float *d_t, int batch, float *grads, size_t n,
+                           double *loss);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8) on a batch; loss before the step. */
+dg_status dg_mlp_train_step(dg_mlp m, const float *d_x, const float *d_t, int batch, double lr, double *loss);
+/* Add the network's output as a modal source to every stage of h (degree 1,
+ * FP32; inputs: the 3 x 4 modes of the element and of its W, E, S, N
+ * neighbours, zeros across a pole; the h mode-0 output is shifted so that the
+ * total mass is unchanged).  m = NULL detaches.  The network must outlive the
+ * attachment. */
+dg_status dg_attach_mlp(dg_handle h, dg_mlp m);
+/* Make the coarse solver's state the cos(theta)-weighted L2 projection of
+ * the fine solver's state (nested meshes: fine nlon = r coarse nlon and fine
+ * nlat = r coarse nlat), computed on the GPU in FP64. */
+dg_status dg_restrict_from(dg_handle coarse, dg_handle fine);
+
+/* ------------------------------------------------------------------------
  * Batched ensemble: many independent meshes of uneven sizes and degrees (the
  * decoupled copies of the 2-D problem of the paper's vertical-levels
  * experiment, Sec. 5.2.2), advanced together in FP32 by one persistent

@@ -95,6 +95,8 @@ struct dg_ctx {
     bool have_state = false;
     long long launches = 0;       // fused stage kernels
     long long aux_launches = 0;   // conversion, mass and wave-speed kernels
+    dg_mlp_ctx *mlp = nullptr;    // learned source term (degree 1, FP32)
+    float *src = nullptr;         // its per-stage modal output
     std::vector<GraphEntry> graphs;
 };
 
@@ -217,6 +219,16 @@ dg_status launch_step_t(dg_ctx *h, double dt, int cur, const RowTab<T> *rows)
         a.cc = (T)pl[s].cc;
         a.cd = (T)pl[s].cd;
         a.dt = (T)dt;
+        if constexpr (sizeof(T) == sizeof(float)) {
+            if (h->mlp) {
+                if (dg_mlp_launch_source(h->mlp, reinterpret_cast<const float *>(a.base),
+                                         reinterpret_cast<const float *>(a.inc), (float)h->href, h->nlon, h->nlat,
+                                         h->c0, h->src, h->stream))
+                    return fail(DG_ECUDA, "learned source launch failed: %s", cudaGetErrorString(cudaGetLastError()));
+                a.src = reinterpret_cast<const T *>(h->src);
+                h->aux_launches += 2;
+            }
+        }
         if (dg_launch_stage<T>(h->n, a, h->stream))
             return fail(DG_ECUDA, "stage kernel launch failed: %s", cudaGetErrorString(cudaGetLastError()));
         h->launches++;
@@ -446,6 +458,7 @@ dg_status dg_destroy(dg_handle h)
     cudaFree(h->d_result);
     cudaFree(h->d_status);
     cudaFree(h->d_maxbits);
+    cudaFree(h->src);
     if (h->own_stream) cudaStreamDestroy(h->own_stream);
     dg_free_tables(h->tab);
     delete h;
@@ -468,6 +481,7 @@ dg_status dg_set_option(dg_handle h, int key, long long value)
             return fail(DG_EUNSUPPORTED, "tensor-core precision %lld is not built", value);
         if (value != DG_PREC_FP64 && value != DG_PREC_FP32) return fail(DG_EINVAL, "unknown precision %lld", value);
         if (value == h->prec) return DG_OK;
+        if (h->mlp) return fail(DG_EINVAL, "detach the learned source (dg_attach_mlp(h, NULL)) first");
         CUDA_TRY(cudaStreamSynchronize(h->stream));
         // carry the resident state over through the FP64 staging buffer
         if (h->have_state) {
@@ -601,6 +615,11 @@ dg_status dg_rhs(dg_handle h, const double *modal_in, double *tend_out, size_t l
         StageArgs<float> a = base_args<float>(h, h->rows32, href);
         a.base = static_cast<float *>(in);
         a.out_rhs = static_cast<float *>(outb);
+        if (h->mlp) {   // the attached learned source is part of the tendency
+            if (dg_mlp_launch_source(h->mlp, a.base, nullptr, (float)href, h->nlon, h->nlat, h->c0, h->src, h->stream))
+                return fail(DG_ECUDA, "learned source launch failed: %s", cudaGetErrorString(cudaGetLastError()));
+            a.src = h->src;
+        }
         r = dg_launch_stage<float>(h->n, a, h->stream);
     }
     if (r) return fail(DG_ECUDA, "stage kernel launch failed: %s", cudaGetErrorString(cudaGetLastError()));
@@ -809,6 +828,66 @@ dg_status dg_project_nodal(dg_handle h, const double *nodal, size_t len_nodal, d
                     }
             }
     }
+    return DG_OK;
+}
+
+dg_status dg_attach_mlp(dg_handle h, dg_mlp m)
+{
+    if (dg_status s = check(h)) return s;
+    DeviceGuard dg(h->device);
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
+    drop_graphs(h);
+    if (!m) {
+        h->mlp = nullptr;
+        return DG_OK;
+    }
+    if (h->p != 1 || h->prec != DG_PREC_FP32)
+        return fail(DG_EUNSUPPORTED, "the learned source needs a degree-1 FP32 solver");
+    if (!dg_mlp_shape_is(m, 60, 128, 12)) return fail(DG_EINVAL, "the learned source needs a 60-128-128-12 network");
+    if (!h->src && cudaMalloc(&h->src, sizeof(float) * h->len) != cudaSuccess)
+        return fail(DG_ENOMEM, "cudaMalloc of the source buffer failed");
+    h->mlp = m;
+    return DG_OK;
+}
+
+dg_status dg_restrict_from(dg_handle coarse, dg_handle fine)
+{
+    if (dg_status s = check(coarse)) return s;
+    if (dg_status s = check(fine)) return s;
+    if (!fine->have_state) return fail(DG_EINVAL, "the fine solver has no state");
+    if (coarse->device != fine->device) return fail(DG_EINVAL, "the solvers live on different devices");
+    const int r = fine->nlon / coarse->nlon;
+    if (r < 1 || fine->nlon != r * coarse->nlon || fine->nlat != r * coarse->nlat)
+        return fail(DG_EINVAL, "the fine mesh must refine every coarse element into r x r elements");
+    if (fine->R != coarse->R) return fail(DG_EINVAL, "different sphere radii");
+    DeviceGuard dg(coarse->device);
+    if (dg_status s = to_api(fine, fine->B[fine->cur], fine->L[fine->cur], fine->stage64, fine->href)) return s;
+    CUDA_TRY(cudaStreamSynchronize(fine->stream));
+    RestrictTab tab;
+    std::memset(&tab, 0, sizeof tab);
+    dg_gauss_legendre(8, tab.x, tab.w);
+    for (int a = 0; a < fine->n; ++a)
+        for (int q = 0; q < 8; ++q) tab.LVf[a][q] = dg_legendre(a, tab.x[q]);
+    tab.jf = 0.25 * fine->tab.dlam * fine->tab.dth;
+    tab.dthc = coarse->tab.dth;
+    tab.inv_jc = 4.0 / (coarse->tab.dlam * coarse->tab.dth);
+    if (dg_launch_restrict(fine->stage64, fine->nlon, fine->n, coarse->stage64, coarse->nlon, coarse->nlat, coarse->n, r,
+                           coarse->rows64, tab, coarse->stream))
+        return fail(DG_ECUDA, "restriction kernel failed: %s", cudaGetErrorString(cudaGetLastError()));
+    coarse->href = 0.0;
+    if (coarse->prec == DG_PREC_FP32) {
+        std::vector<double> m0(coarse->nel);
+        CUDA_TRY(cudaMemcpy2DAsync(m0.data(), sizeof(double), coarse->stage64, sizeof(double) * 3 * coarse->nphi,
+                                   sizeof(double), coarse->nel, cudaMemcpyDeviceToHost, coarse->stream));
+        CUDA_TRY(cudaStreamSynchronize(coarse->stream));
+        double s = 0;
+        for (double v : m0) s += v;
+        coarse->href = 0.5 * s / (double)coarse->nel;
+    }
+    coarse->cur = 0;
+    if (dg_status s = to_internal(coarse, coarse->stage64, coarse->B[0], coarse->L[0], coarse->href)) return s;
+    CUDA_TRY(cudaStreamSynchronize(coarse->stream));
+    coarse->have_state = true;
     return DG_OK;
 }
 

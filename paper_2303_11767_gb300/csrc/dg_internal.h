@@ -82,6 +82,7 @@ struct StageArgs {
     T *acc_out;
     T *out_base;
     T *out_lo;
+    const T *src;    // optional modal source added to k (learned correction)
     const RowTab<T> *rows;
     unsigned int *status;
     int nlon, nlat;
@@ -150,6 +151,23 @@ template <typename T>
 int dg_launch_max_speed(const T *u, int nlon, int nlat, int n, double href, double g,
                         unsigned long long *maxbits, unsigned int *status, void *stream);
 int dg_mass_blocks(size_t nel);
+
+// dg_restrict.cu: nested fine -> coarse projection
+struct RestrictTab {
+    double x[8], w[8];            // 8-point Gauss rule on [-1, 1]
+    double LVf[DG_MAXN][8];       // fine basis L_a at the points
+    double jf;                    // fine element Jacobian (dlam_f / 2)(dth_f / 2)
+    double dthc;                  // coarse dtheta
+    double inv_jc;                // 4 / (dlam_c dth_c)
+};
+int dg_launch_restrict(const double *fine, int fnlon, int fn, double *coarse, int cnlon, int cnlat, int cn, int r,
+                       const RowTab<double> *crows, const RestrictTab &tab, void *stream);
+
+// dg_mlp.cu: the learned source term of a degree-1 solver
+struct dg_mlp_ctx;
+int dg_mlp_launch_source(const dg_mlp_ctx *m, const float *base, const float *inc, float href, int nlon, int nlat,
+                         const double *c0, float *src, void *stream);
+bool dg_mlp_shape_is(const dg_mlp_ctx *m, int nin, int h, int nout);
 
 // dg_api.cpp: set the calling thread's message returned by dg_last_error().
 void dg_set_last_error(const char *msg);

@@ -556,6 +556,15 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &A, int bx, int by
             }
         }
         kk[2][0] = fma(A.P0, rhok, kk[2][0]);
+        if (A.src && valid) {   // learned modal source, same layout as the state
+#pragma unroll
+            for (int f = 0; f < 3; ++f) {
+                T sv[N];
+                load_row<T, N>(A.src + e * EL + f * NP + k * N, sv);
+#pragma unroll
+                for (int a = 0; a < N; ++a) kk[f][a] += sv[a];
+            }
+        }
 
         if (valid) {
             const T cdt = A.cc * A.dt, adt = A.ca * A.dt;

@@ -53,6 +53,19 @@ SIGNATURES = {
     "dg_max_dt_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                          ctypes.c_double, ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p]),
     "dg_last_error": (ctypes.c_char_p, [_H]),
+    "dg_mlp_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_ulonglong,
+                                     ctypes.POINTER(ctypes.c_void_p)]),
+    "dg_mlp_destroy": (ctypes.c_int, [_H]),
+    "dg_mlp_num_params": (ctypes.c_size_t, [_H]),
+    "dg_mlp_get_params": (ctypes.c_int, [_H, ctypes.POINTER(ctypes.c_float), ctypes.c_size_t]),
+    "dg_mlp_set_params": (ctypes.c_int, [_H, ctypes.POINTER(ctypes.c_float), ctypes.c_size_t]),
+    "dg_mlp_set_normalization": (ctypes.c_int, [_H] + [ctypes.POINTER(ctypes.c_float)] * 4),
+    "dg_mlp_forward": (ctypes.c_int, [_H, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
+    "dg_mlp_gradients": (ctypes.c_int, [_H, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                        ctypes.POINTER(ctypes.c_float), ctypes.c_size_t, _dp]),
+    "dg_mlp_train_step": (ctypes.c_int, [_H, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_double, _dp]),
+    "dg_attach_mlp": (ctypes.c_int, [_H, _H]),
+    "dg_restrict_from": (ctypes.c_int, [_H, _H]),
     "dg_ensemble_create": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                           ctypes.POINTER(ctypes.c_int), ctypes.c_double, ctypes.c_double,
                                           ctypes.c_double, ctypes.POINTER(ctypes.c_void_p)]),
@@ -218,6 +231,15 @@ class Solver:
     def stage_launches(self):
         return int(lib().dg_stage_launches(self._h))
 
+    def attach_mlp(self, mlp):
+        """Add the network's output as a learned modal source (None detaches)."""
+        _check(lib().dg_attach_mlp(self._h, mlp._h if mlp is not None else None), self._h)
+        self._mlp = mlp
+
+    def restrict_from(self, fine):
+        """This (coarse) solver's state := projection of `fine`'s state."""
+        _check(lib().dg_restrict_from(self._h, fine._h), self._h)
+
     # -- projection of point values
     def projection_nodes(self):
         lam = np.empty(self.nlon * self.nm)
@@ -322,3 +344,63 @@ class Ensemble:
 
     def stage_launches(self):
         return int(lib().dg_ensemble_stage_launches(self._h))
+
+
+def _fptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+
+
+class MLP:
+    """The per-element network of the learned correction (include/dgswe.h).
+    Device batches are float32 CUDA tensors (anything with data_ptr())."""
+
+    def __init__(self, n_in=60, n_hidden=128, n_out=12, seed=0):
+        h = ctypes.c_void_p()
+        _check(lib().dg_mlp_create(int(n_in), int(n_hidden), int(n_out), int(seed), ctypes.byref(h)))
+        self._h = h
+        self.n_in, self.n_hidden, self.n_out = int(n_in), int(n_hidden), int(n_out)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().dg_mlp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def num_params(self):
+        return int(lib().dg_mlp_num_params(self._h))
+
+    def get_params(self):
+        out = np.empty(self.num_params, dtype=np.float32)
+        _check(lib().dg_mlp_get_params(self._h, _fptr(out), out.size))
+        return out
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        _check(lib().dg_mlp_set_params(self._h, _fptr(p), p.size))
+
+    def set_normalization(self, in_mean, in_std, out_mean, out_std):
+        a = [np.ascontiguousarray(x, dtype=np.float32) for x in (in_mean, in_std, out_mean, out_std)]
+        _check(lib().dg_mlp_set_normalization(self._h, *[_fptr(x) for x in a]))
+
+    def forward(self, x, y):
+        _check(lib().dg_mlp_forward(self._h, ctypes.c_void_p(x.data_ptr()), int(x.shape[0]),
+                                    ctypes.c_void_p(y.data_ptr())))
+
+    def gradients(self, x, t):
+        g = np.empty(self.num_params, dtype=np.float32)
+        loss = ctypes.c_double()
+        _check(lib().dg_mlp_gradients(self._h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(t.data_ptr()),
+                                      int(x.shape[0]), _fptr(g), g.size, ctypes.byref(loss)))
+        return g, loss.value
+
+    def train_step(self, x, t, lr):
+        loss = ctypes.c_double()
+        _check(lib().dg_mlp_train_step(self._h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(t.data_ptr()),
+                                       int(x.shape[0]), float(lr), ctypes.byref(loss)))
+        return loss.value

@@ -1,0 +1,199 @@
+"""Learned correction of a coarse degree-1 DG solver.
+
+A per-element network (60 -> 128 -> 128 -> 12, GELU, BF16 weights, FP32
+accumulation; the library's own kernels) learns the modal tendency that the
+coarse 72 x 36 degree-1 mesh misses, from pairs the method itself generates
+with the degree-4 360 x 180 mesh:
+
+    target = [P(u_fine(t + tau)) - Phi_coarse^tau(P(u_fine(t)))] / tau,
+
+P the nested cos(theta)-weighted L2 projection (5 x 5 fine elements per
+coarse element), Phi_coarse^tau one coarse SSP-RK3 step of size tau.  Inputs:
+the 3 fields x 4 modes of the element and of its W, E, S, N neighbours (zeros
+across a pole), normalised per feature with training statistics.  At run time
+the network's output is added as a modal source in every stage (its h mode-0
+part shifted to keep the total mass), and plain DG is the fallback.
+
+Usage: python -m paper_2303_11767_gb300.learned --pairs 2000 --out result.json
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import time
+
+import numpy as np
+
+from . import dgswe, synth
+
+COARSE = (72, 36, 1)
+FINE = (360, 180, 4)
+CFL_COARSE = 0.1
+CFL_FINE = 0.3
+
+
+def gather_inputs(u):
+    """[nlat, nlon, 3, 4] coarse modal state -> [nlat*nlon, 60] network inputs
+    (element, W, E, S, N; zeros across a pole)."""
+    nlat, nlon = u.shape[:2]
+    e = u.reshape(nlat, nlon, 12)
+    w = np.roll(e, 1, axis=1)
+    ea = np.roll(e, -1, axis=1)
+    s = np.zeros_like(e)
+    s[1:] = e[:-1]
+    n = np.zeros_like(e)
+    n[:-1] = e[1:]
+    return np.concatenate([e, w, ea, s, n], axis=2).reshape(nlat * nlon, 60)
+
+
+class Pair:
+    def __init__(self, seed, spinup_s):
+        self.fine = dgswe.Solver(*FINE, precision="fp32", check_finite=True)
+        self.coarse = dgswe.Solver(*COARSE, precision="fp32", check_finite=True)
+        self.fine.set_option(dgswe.OPT_STEPS_PER_GRAPH, 64)
+        u0 = self.fine.project_grid(synth.SmoothField(seed).fields_grid)
+        self.fine.set_state(u0)
+        self.coarse.restrict_from(self.fine)
+        self.tau = self.coarse.max_dt(CFL_COARSE)
+        self.m = int(math.ceil(self.tau / self.fine.max_dt(CFL_FINE)))
+        self.dt_fine = self.tau / self.m
+        self.advance_fine(int(round(spinup_s / self.tau)))
+
+    def advance_fine(self, coarse_steps):
+        if coarse_steps > 0:
+            self.fine.step(coarse_steps * self.m, self.dt_fine)
+
+    def projected(self):
+        self.coarse.restrict_from(self.fine)
+        return self.coarse.get_state()
+
+    def sample(self, k=1):
+        """(inputs, target) of one pair starting at the current fine time:
+        the mean tendency the coarse mesh misses over k coarse steps,
+        [P(u_fine(t + k tau)) - Phi^k(P(u_fine(t)))] / (k tau)."""
+        self.coarse.restrict_from(self.fine)
+        u0 = self.coarse.get_state()
+        self.coarse.step(k, self.tau)
+        phi = self.coarse.get_state()
+        self.advance_fine(k)
+        u1 = self.projected()
+        return gather_inputs(u0), ((u1 - phi) / (k * self.tau)).reshape(-1, 12)
+
+    def close(self):
+        self.fine.close()
+        self.coarse.close()
+
+
+def generate(n_pairs, seeds, spinup_s=1800.0, stride=4, target_steps=1, log=print):
+    X, T = [], []
+    per = int(math.ceil(n_pairs / len(seeds)))
+    t0 = time.time()
+    for seed in seeds:
+        p = Pair(seed, spinup_s)
+        for k in range(per):
+            if len(X) >= n_pairs:
+                break
+            x, t = p.sample(target_steps)
+            X.append(x)
+            T.append(t)
+            p.advance_fine(max(0, stride - target_steps))   # decorrelate consecutive pairs
+        log(f"seed {seed}: {len(X)} pairs, tau {p.tau:.3f} s, {p.m} fine steps per tau, {time.time() - t0:.0f} s")
+        p.close()
+    return np.concatenate(X).astype(np.float32), np.concatenate(T).astype(np.float32)
+
+
+def train(X, T, epochs=8, batch=4096, lr=1e-3, seed=0, log=print):
+    import torch
+
+    mlp = dgswe.MLP(60, 128, 12, seed=seed)
+    in_mean, in_std = X.mean(0), X.std(0) + 1e-12
+    out_mean, out_std = T.mean(0), T.std(0) + 1e-30
+    mlp.set_normalization(in_mean, in_std, out_mean, out_std)
+    dX = torch.from_numpy(X).cuda()
+    dT = torch.from_numpy(T).cuda()
+    n = X.shape[0]
+    g = torch.Generator(device="cuda")
+    g.manual_seed(seed)
+    history = []
+    steps = 0
+    for ep in range(epochs):
+        perm = torch.randperm(n, device="cuda", generator=g)
+        losses = []
+        for b0 in range(0, n - batch + 1, batch):
+            idx = perm[b0:b0 + batch]
+            xb = dX.index_select(0, idx).contiguous()
+            tb = dT.index_select(0, idx).contiguous()
+            lr_k = lr * 0.5 * (1 + math.cos(math.pi * steps / max(1, epochs * (n // batch))))
+            losses.append(mlp.train_step(xb, tb, lr_k))
+            steps += 1
+        history.append(float(np.mean(losses)))
+        log(f"epoch {ep}: mean normalised MSE {history[-1]:.4f}")
+    return mlp, {"in_mean": in_mean, "in_std": in_std, "out_mean": out_mean, "out_std": out_std}, history
+
+
+def rel_l2(x, y):
+    return [float(np.linalg.norm(x[..., f, :] - y[..., f, :]) / np.linalg.norm(y[..., f, :])) for f in range(3)]
+
+
+def evaluate(mlp, seed, horizon_s, checkpoints=4, spinup_s=1800.0, log=print):
+    """Plain and learned coarse runs from the projected fine state at the end
+    of the spin-up, both compared with the projected fine run."""
+    p = Pair(seed, spinup_s)
+    u0 = p.projected()
+    plain = dgswe.Solver(*COARSE, precision="fp32")
+    learned = dgswe.Solver(*COARSE, precision="fp32")
+    for s in (plain, learned):
+        s.set_state(u0)
+        s.set_option(dgswe.OPT_STEPS_PER_GRAPH, 64)
+    learned.attach_mlp(mlp)
+    nsteps = int(round(horizon_s / p.tau))
+    out = []
+    done = 0
+    for c in range(1, checkpoints + 1):
+        k = nsteps * c // checkpoints - done
+        p.advance_fine(k)
+        plain.step(k, p.tau)
+        learned.step(k, p.tau)
+        done += k
+        ref = p.projected()
+        row = {"hours": done * p.tau / 3600.0, "plain": rel_l2(plain.get_state(), ref),
+               "learned": rel_l2(learned.get_state(), ref),
+               "mass_drift_learned": (learned.total_mass() - plain.total_mass()) / plain.total_mass()}
+        log(json.dumps(row))
+        out.append(row)
+    p.close()
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--pairs", type=int, default=2000)
+    ap.add_argument("--train-seeds", type=int, nargs="+", default=[5000, 5001, 5002, 5003])
+    ap.add_argument("--test-seed", type=int, default=6000)
+    ap.add_argument("--epochs", type=int, default=8)
+    ap.add_argument("--target-steps", type=int, default=1, help="coarse steps the target averages over")
+    ap.add_argument("--stride", type=int, default=4, help="coarse steps between pairs")
+    ap.add_argument("--horizon-hours", type=float, default=12.0)
+    ap.add_argument("--out", default="learned_result.json")
+    ap.add_argument("--params-out", default="")
+    args = ap.parse_args()
+    t0 = time.time()
+    X, T = generate(args.pairs, args.train_seeds, stride=args.stride, target_steps=args.target_steps)
+    t_gen = time.time() - t0
+    mlp, norm, hist = train(X, T, epochs=args.epochs)
+    t_train = time.time() - t0 - t_gen
+    ev = evaluate(mlp, args.test_seed, args.horizon_hours * 3600.0)
+    res = {"pairs": args.pairs, "samples": int(X.shape[0]), "train_seeds": args.train_seeds,
+           "target_steps": args.target_steps, "stride": args.stride,
+           "test_seed": args.test_seed, "epochs": args.epochs, "loss_history": hist, "evaluation": ev,
+           "seconds": {"generate": t_gen, "train": t_train, "evaluate": time.time() - t0 - t_gen - t_train}}
+    with open(args.out, "w") as fh:
+        json.dump(res, fh, indent=1)
+    if args.params_out:
+        np.savez(args.params_out, params=mlp.get_params(), **norm)
+    print(json.dumps(res["evaluation"][-1]))
+
+
+if __name__ == "__main__":
+    main()
