@@ -39,6 +39,11 @@ ENSEMBLE_DESC = ("256 members, nlat uniform on 20..180, nlon = 2 nlat, degree un
 METRIC = "DOF-updates/s per RK stage (FP32/TC/learned vs FP64 plain) at stated L2 error"
 CFL = 0.1
 FLUSH_BYTES = 256 << 20
+# precision -> arithmetic of the path ("+bf16tc": FP32 stage arithmetic with the
+# basis contractions on BF16 tensor cores, FP32 accumulation)
+DTYPES = {"fp32": "f32", "fp64": "f64", "fp32_tc_bf16": "f32+bf16tc", "fp32_tc_fp16": "f32+fp16tc"}
+KERNELS = {"fp32": "stage_kernel<float, N={n}>", "fp64": "stage_kernel<double, N={n}>",
+           "fp32_tc_bf16": "tc_stage_kernel<{n}, bf16>", "fp32_tc_fp16": "tc_stage_kernel<{n}, fp16>"}
 
 
 def parse():
@@ -48,7 +53,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS) + ["c4"])
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--precision", default="fp32", choices=sorted(DTYPES))
     ap.add_argument("--rk-steps", type=int, default=0, help="override RK steps per bench step")
     ap.add_argument("--no-extras", action="store_true", help="skip fp64-plain, e2e and cpu legs (profiling)")
     return ap.parse_args()
@@ -383,24 +388,26 @@ def main():
 
     # dominant kernel: the fused stage; algorithmic bytes per launch = the mean
     # 8/3 state words per DOF of SSP-RK3 (u read by all stages, u^n by two, one write)
-    word = 4 if args.precision == "fp32" else 8
+    word = 8 if args.precision == "fp64" else 4
     bytes_per_launch = dof * word * 8.0 / 3.0
     launch_s = (sum(times) * 1e-3) / max(1, stage_launches_timed)
     peak, peak_kind = peaks()
     achieved = bytes_per_launch / launch_s / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": None, "peak_kind": peak_kind, "kernel": f"stage_kernel<{args.precision}, N={p + 1}>",
+                "traffic": None, "peak_kind": peak_kind, "kernel": KERNELS[args.precision].format(n=p + 1),
                 "bytes_per_launch": bytes_per_launch, "launch_us": launch_s * 1e6}
 
     out = {
         "metric": METRIC, "value": value, "unit": "DOF-updates/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64", "data": "synthetic",
+        "vs_baseline": None, "dtype": DTYPES[args.precision], "data": "synthetic",
         "config": {"workload": desc, "nlon": nlon, "nlat": nlat, "degree": p, "dof": dof,
                    "rk_steps_per_step": nsteps, "dt": dt, "cfl": CFL, "l2": "flushed before every timed step",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "roofline": roofline,
-        "gpu_launches": stage_launches_timed + 2 * args.steps,
+        # + the two mass kernels per step; the tensor-core path also permutes
+        # u^n (base and low parts) into and out of its lane-contiguous layout
+        "gpu_launches": stage_launches_timed + (6 if "tc" in args.precision else 2) * args.steps,
         "clocks": clk.summary(),
         "mass_drift": (m1 - m0) / m0,
     }
@@ -442,7 +449,7 @@ def main():
                                          f"({3 * leg['nsteps']} stages), FP64, {leg['cores']} threads",
                                "seconds": leg["wall"]}
         errs = {}
-        for prec in ("fp32", "fp64"):
+        for prec in sorted({"fp32", "fp64", args.precision}):
             sv = make(prec)
             sv.set_state(leg["u0"])
             sv.step(leg["nsteps"], leg["dt"])

@@ -57,8 +57,12 @@ typedef enum {
 typedef enum {
     DG_PREC_FP64 = 0,           /* all stage arithmetic in FP64 */
     DG_PREC_FP32 = 1,           /* stage arithmetic in FP32, FP64 tables and mass sums */
-    DG_PREC_FP32_TC_BF16 = 2,   /* reserved: BF16 tensor-core contractions */
-    DG_PREC_FP32_TC_FP16 = 3    /* reserved: FP16 tensor-core contractions */
+    DG_PREC_FP32_TC_BF16 = 2,   /* FP32 stage; the basis contractions (modes -> Gauss and
+                                   edge points, volume integral and lift) as BF16 x BF16
+                                   tensor-core GEMMs with FP32 accumulation; C_j^-1, fluxes
+                                   and the RK update in FP32 */
+    DG_PREC_FP32_TC_FP16 = 3    /* the same with FP16 operands (momenta scaled by 2^-5
+                                   into the FP16 range) */
 } dg_precision;
 
 typedef enum {
@@ -268,6 +272,16 @@ long long dg_ensemble_stage_launches(dg_ensemble e);
 #define DG_NOALLOC_MAX_NLAT 8192
 dg_status dg_max_dt_noalloc(const double *d_modal, int nlon, int nlat, int degree, double radius, double g,
                             double cfl, double *d_dt, void *stream);
+
+/* Diagnostic of the tensor-core building block: D = A * B1 for one 128-row
+ * operand, where B1 is the library's eval/trace matrix of degree `degree`
+ * (rows: the (p+1)^2 Gauss points, padded to 8, then the S, N, W, E edge
+ * points) rounded to the operand type `op` (0 BF16, 1 FP16).  d_a is device
+ * FP32 [128][k1] row-major (rounded to the operand type on the way in), d_out
+ * device FP32 [128][n1] row-major; both are caller-owned.  n1 and k1 (host)
+ * receive the padded sizes; with d_a or d_out NULL only the sizes are
+ * returned.  Synchronous.  DG_ETIMEOUT if the tensor cores did not answer. */
+dg_status dg_tc_check_contraction(int degree, int op, const float *d_a, float *d_out, int *n1, int *k1);
 
 /* Number of fused stage-kernel launches issued by this handle so far. */
 long long dg_stage_launches(dg_handle h);

@@ -80,6 +80,9 @@ struct dg_ctx {
     void *L[2] = {nullptr, nullptr};   // low parts of u^n (FP32 path only)
     void *I[2] = {nullptr, nullptr};   // stage increments u_s - u^n
     void *D = nullptr;                 // RK4 accumulator
+    // tensor-core precisions: u^n in the lane-contiguous layout while stepping
+    void *SB[2] = {nullptr, nullptr};
+    void *SL[2] = {nullptr, nullptr};
     int cur = 0;                       // index of B / L holding u^n
     double *stage64 = nullptr;                            // FP64 staging of one state
     RowTab<double> *rows64 = nullptr;
@@ -98,6 +101,8 @@ struct dg_ctx {
     dg_mlp_ctx *mlp = nullptr;    // learned source term (degree 1, FP32)
     float *src = nullptr;         // its per-stage modal output
     std::vector<GraphEntry> graphs;
+    bool f32() const { return prec != DG_PREC_FP64; }                 // FP32 storage
+    bool tc() const { return prec == DG_PREC_FP32_TC_BF16 || prec == DG_PREC_FP32_TC_FP16; }
 };
 
 namespace {
@@ -113,7 +118,8 @@ void drop_graphs(dg_ctx *h)
 
 void free_state_buffers(dg_ctx *h)
 {
-    void **all[] = {&h->B[0], &h->B[1], &h->L[0], &h->L[1], &h->I[0], &h->I[1], &h->D};
+    void **all[] = {&h->B[0], &h->B[1], &h->L[0], &h->L[1], &h->I[0], &h->I[1], &h->D,
+                    &h->SB[0], &h->SB[1], &h->SL[0], &h->SL[1]};
     for (void **u : all) {
         if (*u) cudaFree(*u);
         *u = nullptr;
@@ -124,9 +130,15 @@ dg_status alloc_state_buffers(dg_ctx *h)
 {
     const size_t bytes = h->len * elem_size(h->prec);
     std::vector<void **> want = {&h->B[0], &h->B[1], &h->I[0], &h->I[1], &h->D};
-    if (h->prec == DG_PREC_FP32) {
+    if (h->f32()) {
         want.push_back(&h->L[0]);
         want.push_back(&h->L[1]);
+    }
+    if (h->tc()) {
+        for (int k = 0; k < 2; ++k) {
+            want.push_back(&h->SB[k]);
+            want.push_back(&h->SL[k]);
+        }
     }
     for (void **u : want) {
         if (cudaMalloc(u, bytes) != cudaSuccess) {
@@ -204,15 +216,17 @@ dg_status launch_step_t(dg_ctx *h, double dt, int cur, const RowTab<T> *rows)
     auto I = [&](int i) -> T * { return i < 0 ? nullptr : static_cast<T *>(h->I[i]); };
     for (int s = 0; s < ns; ++s) {
         StageArgs<T> a = base_args<T>(h, rows, h->href);
-        a.base = static_cast<const T *>(h->B[cur]);
         a.inc = I(pl[s].inc_in);
         a.inc_out = I(pl[s].inc_out);
         a.acc_in = pl[s].acc_in >= 0 ? static_cast<const T *>(h->D) : nullptr;
         a.acc_out = pl[s].acc_out >= 0 ? static_cast<T *>(h->D) : nullptr;
+        void *const *Bv = h->tc() ? h->SB : h->B;
+        void *const *Lv = h->tc() ? h->SL : h->L;
+        a.base = static_cast<const T *>(Bv[cur]);
         if (pl[s].fin) {
-            a.lo = static_cast<const T *>(h->L[cur]);
-            a.out_base = static_cast<T *>(h->B[cur ^ 1]);
-            a.out_lo = static_cast<T *>(h->L[cur ^ 1]);
+            a.lo = static_cast<const T *>(Lv[cur]);
+            a.out_base = static_cast<T *>(Bv[cur ^ 1]);
+            a.out_lo = static_cast<T *>(Lv[cur ^ 1]);
         }
         a.ci = (T)pl[s].ci;
         a.ca = (T)pl[s].ca;
@@ -229,10 +243,32 @@ dg_status launch_step_t(dg_ctx *h, double dt, int cur, const RowTab<T> *rows)
                 h->aux_launches += 2;
             }
         }
-        if (dg_launch_stage<T>(h->n, a, h->stream))
-            return fail(DG_ECUDA, "stage kernel launch failed: %s", cudaGetErrorString(cudaGetLastError()));
+        int r;
+        if constexpr (sizeof(T) == sizeof(float)) {
+            r = h->tc() ? dg_launch_stage_tc(h->n, h->prec - DG_PREC_FP32_TC_BF16, a, h->stream)
+                        : dg_launch_stage<T>(h->n, a, h->stream);
+        } else {
+            r = dg_launch_stage<T>(h->n, a, h->stream);
+        }
+        if (r) return fail(DG_ECUDA, "stage kernel launch failed: %s", cudaGetErrorString(cudaGetLastError()));
         h->launches++;
     }
+    return DG_OK;
+}
+
+// Tensor-core precisions: u^n (base and low parts) between the element-major
+// layout of the API-side kernels and the lane-contiguous one of the stage.
+dg_status permute_state(dg_ctx *h, int idx, int to_lanes)
+{
+    const int el = 3 * h->nphi;
+    float *B = static_cast<float *>(h->B[idx]), *L = static_cast<float *>(h->L[idx]);
+    float *SB = static_cast<float *>(h->SB[idx]), *SL = static_cast<float *>(h->SL[idx]);
+    int r = to_lanes ? (dg_launch_permute(B, SB, h->nlat, h->nlon, el, 1, h->stream) ||
+                        dg_launch_permute(L, SL, h->nlat, h->nlon, el, 1, h->stream))
+                     : (dg_launch_permute(SB, B, h->nlat, h->nlon, el, 0, h->stream) ||
+                        dg_launch_permute(SL, L, h->nlat, h->nlon, el, 0, h->stream));
+    if (r) return fail(DG_ECUDA, "layout permutation failed: %s", cudaGetErrorString(cudaGetLastError()));
+    h->aux_launches += 2;
     return DG_OK;
 }
 
@@ -254,6 +290,7 @@ dg_status read_status(dg_ctx *h)
     CUDA_TRY(cudaStreamSynchronize(h->stream));
     if (st) {
         CUDA_TRY(cudaMemsetAsync(h->d_status, 0, sizeof(unsigned), h->stream));
+        if (st & DG_STATUS_TIMEOUT) return fail(DG_ETIMEOUT, "a bounded wait for the tensor cores gave up");
         if (st & DG_STATUS_NONPHYSICAL) return fail(DG_ENONPHYSICAL, "h <= 0 at a quadrature point");
         return fail(DG_ENONFINITE, "non-finite value in the state");
     }
@@ -477,9 +514,10 @@ dg_status dg_set_option(dg_handle h, int key, long long value)
     DeviceGuard dg(h->device);
     switch (key) {
     case DG_OPT_PRECISION: {
-        if (value == DG_PREC_FP32_TC_BF16 || value == DG_PREC_FP32_TC_FP16)
-            return fail(DG_EUNSUPPORTED, "tensor-core precision %lld is not built", value);
-        if (value != DG_PREC_FP64 && value != DG_PREC_FP32) return fail(DG_EINVAL, "unknown precision %lld", value);
+        if (value < DG_PREC_FP64 || value > DG_PREC_FP32_TC_FP16) return fail(DG_EINVAL, "unknown precision %lld", value);
+        if ((value == DG_PREC_FP32_TC_BF16 || value == DG_PREC_FP32_TC_FP16) &&
+            dg_prepare_stage_tc(h->n, (int)(value - DG_PREC_FP32_TC_BF16)))
+            return fail(DG_ECUDA, "tensor-core tables: %s", cudaGetErrorString(cudaGetLastError()));
         if (value == h->prec) return DG_OK;
         if (h->mlp) return fail(DG_EINVAL, "detach the learned source (dg_attach_mlp(h, NULL)) first");
         CUDA_TRY(cudaStreamSynchronize(h->stream));
@@ -494,7 +532,7 @@ dg_status dg_set_option(dg_handle h, int key, long long value)
         if (dg_status s = alloc_state_buffers(h)) return s;
         h->cur = 0;
         if (h->have_state) {
-            if (h->prec == DG_PREC_FP32) {
+            if (h->f32()) {
                 // reference depth: mean of the element mean depths
                 std::vector<double> m0(h->nel);
                 CUDA_TRY(cudaMemcpy2D(m0.data(), sizeof(double), h->stage64, sizeof(double) * 3 * h->nphi,
@@ -545,7 +583,7 @@ dg_status dg_set_state_device(dg_handle h, const double *d_modal, size_t len)
     DeviceGuard dg(h->device);
     CUDA_TRY(cudaMemcpyAsync(h->stage64, d_modal, len * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
     h->href = 0.0;
-    if (h->prec == DG_PREC_FP32) {
+    if (h->f32()) {
         std::vector<double> m0(h->nel);
         CUDA_TRY(cudaMemcpy2DAsync(m0.data(), sizeof(double), h->stage64, sizeof(double) * 3 * h->nphi,
                                    sizeof(double), h->nel, cudaMemcpyDeviceToHost, h->stream));
@@ -566,7 +604,7 @@ dg_status dg_set_state(dg_handle h, const double *modal, size_t len)
     if (!modal || len != h->len) return fail(DG_EINVAL, "state length %zu, expected %zu", len, h->len);
     DeviceGuard dg(h->device);
     CUDA_TRY(cudaMemcpyAsync(h->stage64, modal, len * sizeof(double), cudaMemcpyHostToDevice, h->stream));
-    h->href = h->prec == DG_PREC_FP32 ? mean_depth(modal, h->nel, h->nphi) : 0.0;
+    h->href = h->f32() ? mean_depth(modal, h->nel, h->nphi) : 0.0;
     h->cur = 0;
     if (dg_status s = to_internal(h, h->stage64, h->B[0], h->L[0], h->href)) return s;
     CUDA_TRY(cudaStreamSynchronize(h->stream));   // the host buffer is only borrowed
@@ -602,7 +640,7 @@ dg_status dg_rhs(dg_handle h, const double *modal_in, double *tend_out, size_t l
     DeviceGuard dg(h->device);
     // scratch: the increment buffers are free between steps
     void *in = h->I[0], *outb = h->I[1];
-    const double href = h->prec == DG_PREC_FP32 ? mean_depth(modal_in, h->nel, h->nphi) : 0.0;
+    const double href = h->f32() ? mean_depth(modal_in, h->nel, h->nphi) : 0.0;
     CUDA_TRY(cudaMemcpyAsync(h->stage64, modal_in, len * sizeof(double), cudaMemcpyHostToDevice, h->stream));
     if (dg_status s = to_internal(h, h->stage64, in, nullptr, href)) return s;
     int r;
@@ -611,6 +649,19 @@ dg_status dg_rhs(dg_handle h, const double *modal_in, double *tend_out, size_t l
         a.base = static_cast<double *>(in);
         a.out_rhs = static_cast<double *>(outb);
         r = dg_launch_stage<double>(h->n, a, h->stream);
+    } else if (h->tc()) {
+        // stage in the lane-contiguous layout: input through SB[0], tendency in SB[1]
+        const int el = 3 * h->nphi;
+        if (dg_launch_permute(static_cast<float *>(in), static_cast<float *>(h->SB[0]), h->nlat, h->nlon, el, 1,
+                              h->stream))
+            return fail(DG_ECUDA, "layout permutation failed: %s", cudaGetErrorString(cudaGetLastError()));
+        StageArgs<float> a = base_args<float>(h, h->rows32, href);
+        a.base = static_cast<float *>(h->SB[0]);
+        a.out_rhs = static_cast<float *>(h->SB[1]);
+        r = dg_launch_stage_tc(h->n, h->prec - DG_PREC_FP32_TC_BF16, a, h->stream);
+        if (!r) r = dg_launch_permute(static_cast<float *>(h->SB[1]), static_cast<float *>(outb), h->nlat, h->nlon,
+                                      el, 0, h->stream);
+        h->aux_launches += 2;
     } else {
         StageArgs<float> a = base_args<float>(h, h->rows32, href);
         a.base = static_cast<float *>(in);
@@ -639,6 +690,8 @@ dg_status dg_step(dg_handle h, int n, double dt)
     if (!h->have_state) return fail(DG_EINVAL, "no state set");
     if (n == 0) return DG_OK;
     DeviceGuard dg(h->device);
+    if (h->tc())
+        if (dg_status s = permute_state(h, h->cur, 1)) return s;
     int K = std::min(h->spg, n);
     if ((K & 1) && K > 1) K -= 1;   // even graphs return u^n to the same base buffer
     int full = n / K, rest = n - full * K;
@@ -692,6 +745,8 @@ dg_status dg_step(dg_handle h, int n, double dt)
         if (dg_status st = launch_steps(h, rest, dt, &cur)) return st;
         h->cur = cur;
     }
+    if (h->tc())
+        if (dg_status s = permute_state(h, h->cur, 0)) return s;
     h->t += n * dt;
     if (h->check) return read_status(h);
     return DG_OK;
@@ -875,7 +930,7 @@ dg_status dg_restrict_from(dg_handle coarse, dg_handle fine)
                            coarse->rows64, tab, coarse->stream))
         return fail(DG_ECUDA, "restriction kernel failed: %s", cudaGetErrorString(cudaGetLastError()));
     coarse->href = 0.0;
-    if (coarse->prec == DG_PREC_FP32) {
+    if (coarse->f32()) {
         std::vector<double> m0(coarse->nel);
         CUDA_TRY(cudaMemcpy2DAsync(m0.data(), sizeof(double), coarse->stage64, sizeof(double) * 3 * coarse->nphi,
                                    sizeof(double), coarse->nel, cudaMemcpyDeviceToHost, coarse->stream));
@@ -888,6 +943,20 @@ dg_status dg_restrict_from(dg_handle coarse, dg_handle fine)
     if (dg_status s = to_internal(coarse, coarse->stage64, coarse->B[0], coarse->L[0], coarse->href)) return s;
     CUDA_TRY(cudaStreamSynchronize(coarse->stream));
     coarse->have_state = true;
+    return DG_OK;
+}
+
+dg_status dg_tc_check_contraction(int degree, int op, const float *d_a, float *d_out, int *n1, int *k1)
+{
+    if (degree < 0 || degree > DG_MAXN - 1 || (op != 0 && op != 1) || !n1 || !k1)
+        return fail(DG_EINVAL, "need 0 <= degree <= %d, op 0 or 1, n1 and k1", DG_MAXN - 1);
+    cudaStream_t s = nullptr;
+    if (d_a && d_out && cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess)
+        return fail(DG_ECUDA, "stream creation failed");
+    int r = dg_tc_gemm_check(degree + 1, op, d_a, d_out, n1, k1, s);
+    if (s) cudaStreamDestroy(s);
+    if (r == 2) return fail(DG_ETIMEOUT, "the tensor cores did not complete the contraction");
+    if (r) return fail(DG_ECUDA, "contraction check failed: %s", cudaGetErrorString(cudaGetLastError()));
     return DG_OK;
 }
 

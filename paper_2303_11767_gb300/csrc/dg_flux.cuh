@@ -1,0 +1,92 @@
+// dg_flux.cuh -- pointwise physics shared by the stage kernels: the fluxes
+// of the shallow water system on the sphere (paper Eq. sph3) and the Rusanov
+// flux (Eq. rusanov), with h stored relative to a reference depth.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "dg_internal.h"
+
+namespace dgk {
+
+template <typename T>
+__device__ __forceinline__ T rcp(T x);
+template <>
+__device__ __forceinline__ double rcp<double>(double x) { return 1.0 / x; }
+// FP32: the SFU reciprocal (<= 2 ulp), far inside the FP32 tolerance
+template <>
+__device__ __forceinline__ float rcp<float>(float x) { return __fdividef(1.0f, x); }
+
+template <typename T>
+__device__ __forceinline__ T wave_sqrt(T x);
+template <>
+__device__ __forceinline__ double wave_sqrt<double>(double x) { return sqrt(x); }
+// FP32: x * rsqrt(x) on the SFU; only feeds the Rusanov dissipation speed
+template <>
+__device__ __forceinline__ float wave_sqrt<float>(float x) { return x * rsqrtf(x); }
+
+// h <= 0 makes u = hu/h meaningless; a NaN depth is reported as non-finite.
+template <typename T>
+__device__ __forceinline__ void check_depth(T h, unsigned &st)
+{
+    if (!(h > T(0))) st |= (h != h) ? DG_STATUS_NONFINITE : DG_STATUS_NONPHYSICAL;
+}
+
+// Physical lambda-flux (hu, hu u + P, hu v) of a state q = (h', hu, hv) with
+// h = href + h' and the pressure P = g h' (href + h'/2) (the constant part
+// g href^2/2 is carried by the rho table), and the wave speed |u| + sqrt(g h).
+template <typename T>
+__device__ __forceinline__ void lam_flux(const T *q, T href, T g, T *f, T &speed, unsigned &st)
+{
+    const T h = href + q[0];
+    check_depth(h, st);
+    const T u = q[1] * rcp(h);
+    const T P = q[0] * g * (href + T(0.5) * q[0]);
+    f[0] = q[1];
+    f[1] = q[1] * u + P;
+    f[2] = q[2] * u;
+    speed = fabs(u) + wave_sqrt(g * h);
+}
+
+template <typename T>
+__device__ __forceinline__ void th_flux(const T *q, T href, T g, T *f, T &speed, unsigned &st)
+{
+    const T h = href + q[0];
+    check_depth(h, st);
+    const T v = q[2] * rcp(h);
+    const T P = q[0] * g * (href + T(0.5) * q[0]);
+    f[0] = q[2];
+    f[1] = q[1] * v;
+    f[2] = q[2] * v + P;
+    speed = fabs(v) + wave_sqrt(g * h);
+}
+
+// Rusanov flux through a lambda-face, left state L (west), right state R
+// (east): F* = (F(L) + F(R))/2 - alpha/2 (R - L) with alpha the larger
+// one-sided |u| + c; the cos(theta) of U = cos(theta) q cancels against the
+// 1/cos(theta) of the eigenvalue of dF/dU.  Scaled by cF = 2/(R dlambda).
+template <typename T>
+__device__ __forceinline__ void rusanov_lam(const T *L, const T *R, T href, T g, T cF, T *out, unsigned &st)
+{
+    T fl[3], fr[3], al, ar;
+    lam_flux(L, href, g, fl, al, st);
+    lam_flux(R, href, g, fr, ar, st);
+    const T a = fmax(al, ar);
+#pragma unroll
+    for (int f = 0; f < 3; ++f) out[f] = cF * (T(0.5) * (fl[f] + fr[f]) - T(0.5) * a * (R[f] - L[f]));
+}
+
+// Rusanov flux through a theta-face, lower state S, upper state N, times the
+// edge cos(theta) ce (flux and jump of U both carry it); scaled by cG.
+template <typename T>
+__device__ __forceinline__ void rusanov_th(const T *S, const T *Nq, T href, T g, T cGce, T *out, unsigned &st)
+{
+    T fs[3], fn[3], as, an;
+    th_flux(S, href, g, fs, as, st);
+    th_flux(Nq, href, g, fn, an, st);
+    const T a = fmax(as, an);
+#pragma unroll
+    for (int f = 0; f < 3; ++f) out[f] = cGce * (T(0.5) * (fs[f] + fn[f]) - T(0.5) * a * (Nq[f] - S[f]));
+}
+
+}  // namespace dgk

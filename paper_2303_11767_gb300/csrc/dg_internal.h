@@ -130,11 +130,26 @@ int dg_ensemble_tile_width(int n);   // elements per warp for degree n - 1
 // status bits written by device code
 #define DG_STATUS_NONPHYSICAL 1u
 #define DG_STATUS_NONFINITE 2u
+#define DG_STATUS_TIMEOUT 4u      // a bounded wait on the tensor cores gave up
 
 template <typename T>
 int dg_launch_stage(int n, const StageArgs<T> &a, void *stream);
 template <typename T>
 int dg_upload_basis(const BasisTab<double> *all);   // all[n-1] for n = 1..DG_MAXN
+
+// dg_tc.cu: the stage with the basis contractions on the tensor cores
+// (tcgen05; op 0 = BF16, 1 = FP16 operands, FP32 accumulation).  The state
+// arrays are in the lane-contiguous layout [lat][field][mode][lon].
+int dg_launch_stage_tc(int n, int op, const StageArgs<float> &a, void *stream);
+// Upload the tensor-core tables of (n, op) and set the kernel's shared-memory
+// opt-in on the current device (outside any stream capture); 0 on success.
+int dg_prepare_stage_tc(int n, int op);
+// [lat][lon][field][mode] <-> [lat][field][mode][lon] (to_lanes = 1: first to second)
+int dg_launch_permute(const float *src, float *dst, int nlat, int nlon, int el, int to_lanes, void *stream);
+// tensor-core contraction check: D = A * B1 for a 128-row operand A
+// (row-major [128][K1]) with the degree's eval/trace matrix; d is [128][N1]
+// row-major in FP32, and n1 / k1 receive the padded sizes.
+int dg_tc_gemm_check(int n, int op, const float *a, float *d, int *n1, int *k1, void *stream);
 
 // dg_aux.cu
 // FP64 API layout <-> internal (base, lo) with h stored relative to href; lo

@@ -1,0 +1,995 @@
+// dg_tc.cu -- the fused RK stage with the basis contractions on the tensor
+// cores of sm_103a: tcgen05.mma with BF16 or FP16 operands staged in shared
+// memory and FP32 accumulators in tensor memory (TMEM).
+//
+// The element operator of paper Eq. (dg_parts) with the orthonormal Legendre
+// basis is written as dense per-element maps:
+//   GEMM1  modes -> values at the n x n Gauss points and at the 4n edge
+//          points (S, N, W, E), one MMA per field over 128 elements;
+//   GEMM2  [F | G | S | edge fluxes] -> the modal residual before the inverse
+//          mass matrix, one MMA per field;
+// the pointwise fluxes and sources (Eq. sph3), the Rusanov flux (Eq.
+// rusanov, zero at the poles), the inverse of the per-row mass matrix C_j
+// (Eq. ode) and the Runge-Kutta combination (Table Butcher) run on the CUDA
+// cores in FP32.
+//
+// Thread mapping: thread = element.  A warp is one latitude row of the tile:
+// lane 0 holds the element west of the tile, lanes 1..30 the interior, the
+// lane after the last interior one the element east of it.  An MMA row is a
+// TMEM lane, so every thread reads the accumulators of its own element.  The
+// rows south and north of the tile go through a third MMA that produces only
+// their edge traces.  The state arrays are lane-contiguous,
+// [lat][field][mode][lon], so every global load and store of a warp is one
+// contiguous segment.
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include <cstdint>
+#include <cstring>
+#include <vector>
+
+#include "dg_internal.h"
+#include "dg_flux.cuh"
+
+namespace {
+
+constexpr int TC_TW = 30;            // interior elements of a warp row
+constexpr uint32_t CH = 2048;        // bytes of one 8-wide K chunk of a 128-row operand
+constexpr uint32_t TMEM_COLS = 256;  // tensor-memory columns of one CTA (two CTAs per SM)
+constexpr int WAIT_LIMIT = 1 << 22;  // bounded wait for the tensor cores
+
+// Padded sizes of the per-element maps for n = p + 1 points per direction.
+//   GEMM1: K1 modes (NP, padded to 16) -> N1 columns: NC node columns (NP
+//          padded to 8), then the 4n traces S, N, W, E (n each)
+//   GEMM2: K2 = 8 * KC2 inputs: chunks [0, CN) F, [CN, 2CN) G, [2CN, 3CN) S,
+//          then CE chunks of edge fluxes (W, E, S, N, EW slots each)
+//          -> N2 output modes (NP padded to 16)
+template <int N>
+struct TcGeo {
+    static constexpr int NP = N * N;
+    static constexpr int CN = (NP + 7) / 8;
+    static constexpr int NC = 8 * CN;
+    static constexpr int K1 = 16 * ((NP + 15) / 16);
+    static constexpr int K1C = K1 / 8;
+    static constexpr int N1 = 16 * ((NC + (4 * N > 16 ? 4 * N : 16) + 15) / 16);
+    static constexpr int N2 = 16 * ((NP + 15) / 16);
+    static constexpr int EW = N <= 4 ? 4 : 8;
+    static constexpr int CE = 4 * EW / 8;
+    static constexpr int KC2 = ((3 * CN + CE + 1) / 2) * 2;
+    static constexpr int K2 = 8 * KC2;
+    static constexpr int TRC = (4 * N + 7) / 8 * 8;   // trace columns read back
+};
+
+// 128-row M tiles per CTA: two for n <= 4 (8 warps), one for n = 5 (its
+// three fields of 64 accumulator columns fill the CTA's share of TMEM).
+template <int N>
+constexpr int tc_qm()
+{
+    return N == 5 ? 1 : 2;
+}
+
+// Shared-memory plan (bytes).  A1 / A1h (GEMM1 operands of the tile and of
+// the halo rows) are dead once GEMM1 has completed, so GEMM2's operand A2
+// reuses the region; the row exchange buffers XN / XS live in node chunks of
+// A2 that are written only after the exchange.
+template <int N, int QM>
+struct TcSmem {
+    using GE = TcGeo<N>;
+    static constexpr uint32_t B1 = 0;
+    static constexpr uint32_t SZ_B1 = GE::N1 * GE::K1 * 2;
+    static constexpr uint32_t B2 = (SZ_B1 + 127) / 128 * 128;
+    static constexpr uint32_t SZ_B2 = GE::N2 * GE::K2 * 2;
+    static constexpr uint32_t A = (B2 + SZ_B2 + 1023) / 1024 * 1024;
+    static constexpr uint32_t SZ_A1 = QM * 3 * GE::K1C * CH;
+    static constexpr uint32_t SZ_A1H = 3 * GE::K1C * CH;
+    static constexpr uint32_t SZ_A2 = QM * 3 * GE::KC2 * CH;
+    static constexpr uint32_t SZ_A = SZ_A1 + SZ_A1H > SZ_A2 ? SZ_A1 + SZ_A1H : SZ_A2;
+    static constexpr uint32_t BYTES = A + SZ_A;
+    static constexpr uint32_t XN = A;                   // tile 0, field 0, node chunks
+    static constexpr uint32_t XS = A + GE::KC2 * CH;    // tile 0, field 1, node chunks
+    static constexpr uint32_t SZ_X = 4 * QM * 32 * 3 * N * 4;
+    static_assert(SZ_X <= 3 * GE::CN * CH, "row exchange exceeds the node chunks");
+    static_assert(QM * 3 * GE::N1 + 48 <= (int)TMEM_COLS, "tensor-memory columns");
+    static_assert(BYTES <= 113 * 1024, "two CTAs per SM");
+};
+
+template <typename OpT>
+struct Op;
+template <>
+struct Op<__nv_bfloat16> {
+    static constexpr bool bf16 = true;
+    static constexpr float mom_scale = 1.0f;
+    __device__ static uint32_t pack(float a, float b)
+    {
+        __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
+        return *reinterpret_cast<uint32_t *>(&v);
+    }
+    static uint16_t host_bits(float x)
+    {
+        __nv_bfloat16 v = __float2bfloat16_rn(x);
+        uint16_t u;
+        std::memcpy(&u, &v, 2);
+        return u;
+    }
+};
+template <>
+struct Op<__half> {
+    static constexpr bool bf16 = false;
+    // momenta of up to 2^21 m^2/s stay inside the FP16 range; a power of two,
+    // so the scaling itself is exact
+    static constexpr float mom_scale = 1.0f / 32.0f;
+    __device__ static uint32_t pack(float a, float b)
+    {
+        __half2 v = __floats2half2_rn(a, b);
+        return *reinterpret_cast<uint32_t *>(&v);
+    }
+    static uint16_t host_bits(float x)
+    {
+        __half v = __float2half_rn(x);
+        uint16_t u;
+        std::memcpy(&u, &v, 2);
+        return u;
+    }
+};
+
+// ------------------------------------------------------------ PTX helpers --
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// Shared-memory matrix descriptor, no swizzle, K-major: core matrices of 8
+// rows x 16 bytes; lbo = byte distance of K-adjacent core matrices, sbo = of
+// row-adjacent (M or N) ones.
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo)
+{
+    uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFFu);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;   // descriptor version of the 5th-generation tensor cores
+    return d;
+}
+
+// Instruction descriptor of kind::f16: FP32 accumulator, A and B of the same
+// 16-bit type, both K-major, M x N.
+template <bool BF16>
+__host__ __device__ constexpr uint32_t idesc(int M, int N)
+{
+    return (1u << 4) | ((BF16 ? 1u : 0u) << 7) | ((BF16 ? 1u : 0u) << 10) | ((uint32_t)(N >> 3) << 17) |
+           ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t id, uint32_t acc)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(id), "r"(acc));
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t mbar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t mbar)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// Wait for phase `parity` of the barrier, giving up after WAIT_LIMIT polls.
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity)
+{
+    for (int it = 0; it < WAIT_LIMIT; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}\n"
+            : "=r"(done)
+            : "r"(mbar), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void tmem_alloc(uint32_t slot)
+{
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(slot), "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr)
+{
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(TMEM_COLS) : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// 8 consecutive accumulator columns of the thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float *v)
+{
+    uint32_t r0, r1, r2, r3, r4, r5, r6, r7;
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3), "=r"(r4), "=r"(r5), "=r"(r6), "=r"(r7)
+                 : "r"(taddr));
+    v[0] = __uint_as_float(r0);
+    v[1] = __uint_as_float(r1);
+    v[2] = __uint_as_float(r2);
+    v[3] = __uint_as_float(r3);
+    v[4] = __uint_as_float(r4);
+    v[5] = __uint_as_float(r5);
+    v[6] = __uint_as_float(r6);
+    v[7] = __uint_as_float(r7);
+}
+
+__device__ __forceinline__ void tmem_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// Ties 8 registers to the point after tmem_wait(): no use of them can be
+// scheduled before the loads have landed.
+__device__ __forceinline__ void reg_fence8(float *v)
+{
+    asm volatile("" : "+f"(v[0]), "+f"(v[1]), "+f"(v[2]), "+f"(v[3]), "+f"(v[4]), "+f"(v[5]), "+f"(v[6]), "+f"(v[7]));
+}
+
+template <typename OpT>
+__device__ __forceinline__ void put_chunk(unsigned char *p, const float *v)
+{
+    uint4 u;
+    u.x = Op<OpT>::pack(v[0], v[1]);
+    u.y = Op<OpT>::pack(v[2], v[3]);
+    u.z = Op<OpT>::pack(v[4], v[5]);
+    u.w = Op<OpT>::pack(v[6], v[7]);
+    *reinterpret_cast<uint4 *>(p) = u;
+}
+
+// ------------------------------------------------------------ stage kernel --
+
+template <int N, typename OpT, int QM>
+__global__ void __launch_bounds__(128 * QM, 2) tc_stage_kernel(const StageArgs<float> A, const uint4 *__restrict__ gB1,
+                                                            const uint4 *__restrict__ gB2)
+{
+    using GE = TcGeo<N>;
+    using SM = TcSmem<N, QM>;
+    constexpr int NP = GE::NP, CN = GE::CN, NC = GE::NC, K1C = GE::K1C, N1 = GE::N1, N2 = GE::N2, EW = GE::EW,
+                  KC2 = GE::KC2, TRC = GE::TRC;
+    constexpr int NT = 128 * QM, ROWS = 4 * QM;
+    constexpr float MS = Op<OpT>::mom_scale, IMS = 1.0f / Op<OpT>::mom_scale;
+    extern __shared__ __align__(128) unsigned char sm[];
+    __shared__ __align__(8) uint64_t mbar;
+    __shared__ uint32_t tslot;
+
+    const int tid = threadIdx.x, w = tid >> 5, l = tid & 31;
+    const int tt = w >> 2, q4 = w & 3;   // M tile of the warp and its TMEM lane quarter
+    const int i0 = blockIdx.x * TC_TW, j0 = blockIdx.y * ROWS;
+    const int Gv = min(TC_TW, A.nlon - i0), Wv = min(ROWS, A.nlat - j0);
+    const bool row_ok = w < Wv;
+    const int j = row_ok ? j0 + w : j0;   // rows past the mesh borrow the first row's tables
+    const bool lane_ok = l <= Gv + 1;
+    const bool interior = row_ok && l >= 1 && l <= Gv;
+    const int i = ((i0 + l - 1) % A.nlon + A.nlon) % A.nlon;
+    const size_t rowlen = (size_t)3 * NP * A.nlon;
+    const float href = A.href, gg = A.g;
+    unsigned st = 0, st_int = 0;   // status of any thread / of interior elements only
+    const uint32_t rowoff = (uint32_t)(32 * q4 + l) * 16;
+    unsigned char *const opA = sm + SM::A;
+
+    if (w == 0) tmem_alloc(smem_u32(&tslot));
+    if (tid == 0) mbar_init(smem_u32(&mbar));
+    for (int c = tid; c < (int)(SM::SZ_B1 / 16); c += NT) reinterpret_cast<uint4 *>(sm + SM::B1)[c] = __ldg(gB1 + c);
+    for (int c = tid; c < (int)(SM::SZ_B2 / 16); c += NT) reinterpret_cast<uint4 *>(sm + SM::B2)[c] = __ldg(gB2 + c);
+
+    // ---- S0: stage state u = base + inc of one field of one element -> the
+    //      element's row of a GEMM1 operand (zeros for missing elements)
+    auto stage_field = [&](int jj, bool ok, int f, unsigned char *dst) {
+        float v[8 * K1C];
+#pragma unroll
+        for (int m = 0; m < 8 * K1C; ++m) v[m] = 0.0f;
+        if (ok) {
+            const size_t o0 = (size_t)jj * rowlen + (size_t)f * NP * A.nlon + i;
+#pragma unroll
+            for (int m = 0; m < NP; ++m) v[m] = __ldg(A.base + o0 + (size_t)m * A.nlon);
+            if (A.inc) {
+#pragma unroll
+                for (int m = 0; m < NP; ++m) v[m] += __ldg(A.inc + o0 + (size_t)m * A.nlon);
+            }
+            const float s = f == 0 ? 1.0f : MS;
+#pragma unroll
+            for (int m = 0; m < NP; ++m) v[m] *= s;
+        }
+#pragma unroll
+        for (int c = 0; c < K1C; ++c) put_chunk<OpT>(dst + c * CH, v + 8 * c);
+    };
+#pragma unroll
+    for (int f = 0; f < 3; ++f)
+        stage_field(j0 + w, row_ok && lane_ok, f, opA + (uint32_t)((tt * 3 + f) * K1C) * CH + rowoff);
+    // halo rows: job = side * 3 + f; side 0 = the row south of the tile
+    // (TMEM quarter 0), side 1 = the row north of it (quarter 3)
+    for (int job = w; job < 6; job += ROWS) {
+        const int side = job / 3, f = job - 3 * side;
+        const int jj = side ? j0 + ROWS : j0 - 1;
+        const bool ok = lane_ok && (side ? jj < A.nlat : jj >= 0);
+        stage_field(ok ? jj : 0, ok, f, opA + SM::SZ_A1 + (uint32_t)(f * K1C) * CH + (uint32_t)((side ? 96 : 0) + l) * 16);
+    }
+
+    fence_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tbase = tslot;
+    const uint32_t mb = smem_u32(&mbar);
+    const uint32_t a0 = smem_u32(opA);
+
+    // ---- S1 + S4 on the tensor cores: values at the Gauss and edge points
+    if (tid == 0) {
+        const uint32_t b1 = smem_u32(sm + SM::B1);
+        constexpr uint32_t LB1 = N1 * 16;
+        constexpr uint32_t id1 = idesc<Op<OpT>::bf16>(128, N1), idh = idesc<Op<OpT>::bf16>(128, 16);
+        for (int t = 0; t < QM; ++t)
+            for (int f = 0; f < 3; ++f)
+                for (int s = 0; s < K1C / 2; ++s)
+                    mma(tbase + (uint32_t)((t * 3 + f) * N1), sdesc(a0 + (uint32_t)((t * 3 + f) * K1C + 2 * s) * CH, CH, 128),
+                        sdesc(b1 + 2 * s * LB1, LB1, 128), id1, s > 0);
+        for (int f = 0; f < 3; ++f)
+            for (int s = 0; s < K1C / 2; ++s)
+                mma(tbase + (uint32_t)(QM * 3 * N1 + 16 * f),
+                    sdesc(a0 + SM::SZ_A1 + (uint32_t)(f * K1C + 2 * s) * CH, CH, 128),
+                    sdesc(b1 + NC * 16 + 2 * s * LB1, LB1, 128), idh, s > 0);
+        mma_commit(mb);
+    }
+    if (!mbar_wait(mb, 0)) st |= DG_STATUS_TIMEOUT;
+    tc_fence_after();
+    __syncwarp();
+
+    const uint32_t tl = tbase + ((uint32_t)(32 * q4) << 16);
+
+    // own traces: [0, N) S, [N, 2N) N, [2N, 3N) W, [3N, 4N) E
+    float tr[3][TRC];
+#pragma unroll
+    for (int f = 0; f < 3; ++f)
+#pragma unroll
+        for (int c = 0; c < TRC / 8; ++c) tmem_ld8(tl + (uint32_t)((tt * 3 + f) * N1 + NC + 8 * c), &tr[f][8 * c]);
+    tmem_wait();
+#pragma unroll
+    for (int f = 0; f < 3; ++f)
+#pragma unroll
+        for (int c = 0; c < TRC / 8; ++c) reg_fence8(&tr[f][8 * c]);
+#pragma unroll
+    for (int k = 0; k < TRC; ++k) {
+        tr[1][k] *= IMS;
+        tr[2][k] *= IMS;
+    }
+    // halo traces: warp 0 the N trace of the row south of the tile, the last
+    // warp the S trace of the row north of it
+    float halo[3][N];
+    if (w == 0 || w == ROWS - 1) {
+        float hv[3][16];
+#pragma unroll
+        for (int f = 0; f < 3; ++f) {
+            tmem_ld8(tl + (uint32_t)(QM * 3 * N1 + 16 * f), hv[f]);
+            tmem_ld8(tl + (uint32_t)(QM * 3 * N1 + 16 * f + 8), hv[f] + 8);
+        }
+        tmem_wait();
+#pragma unroll
+        for (int f = 0; f < 3; ++f) {
+            reg_fence8(hv[f]);
+            reg_fence8(hv[f] + 8);
+        }
+#pragma unroll
+        for (int f = 0; f < 3; ++f)
+#pragma unroll
+            for (int k = 0; k < N; ++k) halo[f][k] = (w == 0 ? hv[f][N + k] : hv[f][k]) * (f == 0 ? 1.0f : IMS);
+    } else {
+#pragma unroll
+        for (int f = 0; f < 3; ++f)
+#pragma unroll
+            for (int k = 0; k < N; ++k) halo[f][k] = 0.0f;
+    }
+
+    unsigned char *const a2row = opA + rowoff;
+    auto a2 = [&](int f, int c) { return a2row + (uint32_t)((tt * 3 + f) * KC2 + c) * CH; };
+
+    // ---- S5 lambda faces: lanes 1..Gv+1 evaluate their W edge (the last one
+    //      is the tile's east boundary); the E edge is the next lane's W edge
+    {
+        float efW[3][N], efE[3][N];
+        unsigned sw = 0;
+#pragma unroll
+        for (int k = 0; k < N; ++k) {
+            float L[3], R[3], o[3];
+#pragma unroll
+            for (int f = 0; f < 3; ++f) {
+                L[f] = __shfl_up_sync(0xffffffffu, tr[f][3 * N + k], 1);
+                R[f] = tr[f][2 * N + k];
+            }
+            dgk::rusanov_lam(L, R, href, gg, A.cF, o, sw);
+#pragma unroll
+            for (int f = 0; f < 3; ++f) efW[f][k] = o[f];
+        }
+#pragma unroll
+        for (int f = 0; f < 3; ++f)
+#pragma unroll
+            for (int k = 0; k < N; ++k) efE[f][k] = __shfl_down_sync(0xffffffffu, efW[f][k], 1);
+        if (row_ok && l >= 1 && l <= Gv + 1) st_int |= sw;
+#pragma unroll
+        for (int f = 0; f < 3; ++f) {
+            float c0[8], c1[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) c0[k] = c1[k] = 0.0f;
+#pragma unroll
+            for (int k = 0; k < N; ++k) {
+                c0[k] = efW[f][k];
+                if (EW == 4) c0[4 + k] = efE[f][k];
+                else c1[k] = efE[f][k];
+            }
+            put_chunk<OpT>(a2(f, 3 * CN), c0);
+            if (EW == 8) put_chunk<OpT>(a2(f, 3 * CN + 1), c1);
+#pragma unroll
+            for (int c = 3 * CN + GE::CE; c < KC2; ++c) {   // zero K padding
+                float z[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+                put_chunk<OpT>(a2(f, c), z);
+            }
+        }
+    }
+
+    // ---- S5 theta faces through the row exchange: every element evaluates
+    //      its S edge; its N edge is the S edge of the element above (or,
+    //      for the top row of the tile, is evaluated against the halo row)
+    float *XN = reinterpret_cast<float *>(sm + SM::XN);
+    float *XS = reinterpret_cast<float *>(sm + SM::XS);
+#pragma unroll
+    for (int f = 0; f < 3; ++f)
+#pragma unroll
+        for (int k = 0; k < N; ++k) XN[((w * 3 + f) * N + k) * 32 + l] = tr[f][N + k];
+    __syncthreads();
+    float efS[3][N], efN[3][N];
+    {
+        float nb[3][N];
+#pragma unroll
+        for (int f = 0; f < 3; ++f)
+#pragma unroll
+            for (int k = 0; k < N; ++k) nb[f][k] = w > 0 ? XN[(((w - 1) * 3 + f) * N + k) * 32 + l] : halo[f][k];
+        const float cgs = A.cG * __ldg(&A.rows[j].ce_s);
+        unsigned ss = 0;
+#pragma unroll
+        for (int k = 0; k < N; ++k) {
+            float Sq[3], Nq[3], o[3];
+#pragma unroll
+            for (int f = 0; f < 3; ++f) {
+                Sq[f] = nb[f][k];
+                Nq[f] = tr[f][k];
+            }
+            dgk::rusanov_th(Sq, Nq, href, gg, cgs, o, ss);
+#pragma unroll
+            for (int f = 0; f < 3; ++f) efS[f][k] = j0 + w > 0 ? o[f] : 0.0f;   // pole edge: zero flux
+        }
+        if (interior && j0 + w > 0) st_int |= ss;
+    }
+#pragma unroll
+    for (int f = 0; f < 3; ++f)
+#pragma unroll
+        for (int k = 0; k < N; ++k) XS[((w * 3 + f) * N + k) * 32 + l] = efS[f][k];
+    __syncthreads();
+    if (w + 1 < Wv) {
+#pragma unroll
+        for (int f = 0; f < 3; ++f)
+#pragma unroll
+            for (int k = 0; k < N; ++k) efN[f][k] = XS[(((w + 1) * 3 + f) * N + k) * 32 + l];
+    } else if (j0 + w + 1 >= A.nlat) {
+#pragma unroll
+        for (int f = 0; f < 3; ++f)
+#pragma unroll
+            for (int k = 0; k < N; ++k) efN[f][k] = 0.0f;   // pole edge (or a row past the mesh)
+    } else {   // the last warp of a full tile: its N neighbours are the halo row
+        const float cgn = A.cG * __ldg(&A.rows[j].ce_n);
+        unsigned sn = 0;
+#pragma unroll
+        for (int k = 0; k < N; ++k) {
+            float Sq[3], Nq[3], o[3];
+#pragma unroll
+            for (int f = 0; f < 3; ++f) {
+                Sq[f] = tr[f][N + k];
+                Nq[f] = halo[f][k];
+            }
+            dgk::rusanov_th(Sq, Nq, href, gg, cgn, o, sn);
+#pragma unroll
+            for (int f = 0; f < 3; ++f) efN[f][k] = o[f];
+        }
+        if (interior) st_int |= sn;
+    }
+    __syncthreads();   // the exchange buffers turn back into operand chunks
+#pragma unroll
+    for (int f = 0; f < 3; ++f) {
+        float c0[8], c1[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) c0[k] = c1[k] = 0.0f;
+#pragma unroll
+        for (int k = 0; k < N; ++k) {
+            c0[k] = efS[f][k];
+            if (EW == 4) c0[4 + k] = efN[f][k];
+            else c1[k] = efN[f][k];
+        }
+        if (EW == 4) put_chunk<OpT>(a2(f, 3 * CN + 1), c0);
+        else {
+            put_chunk<OpT>(a2(f, 3 * CN + 2), c0);
+            put_chunk<OpT>(a2(f, 3 * CN + 3), c1);
+        }
+    }
+
+    // ---- S2 pointwise fluxes and sources at the Gauss points, 8 at a time
+    {
+        float cs[N], sn[N];
+#pragma unroll
+        for (int b = 0; b < N; ++b) {
+            cs[b] = __ldg(&A.rows[j].cosn[b]);
+            sn[b] = __ldg(&A.rows[j].sinn[b]);
+        }
+        unsigned sq = 0;
+#pragma unroll
+        for (int g = 0; g < CN; ++g) {
+            float x[3][8];
+#pragma unroll
+            for (int f = 0; f < 3; ++f) tmem_ld8(tl + (uint32_t)((tt * 3 + f) * N1 + 8 * g), x[f]);
+            tmem_wait();
+#pragma unroll
+            for (int f = 0; f < 3; ++f) reg_fence8(x[f]);
+            float Fv[3][8], Gq[3][8], Sv[3][8];
+#pragma unroll
+            for (int qq = 0; qq < 8; ++qq) {
+                const int q = 8 * g + qq;
+                if (q < NP) {
+                    const int be = q / N;
+                    const float hp = x[0][qq], hu = x[1][qq] * IMS, hv = x[2][qq] * IMS;
+                    const float h = href + hp;
+                    dgk::check_depth(h, sq);
+                    const float rh = dgk::rcp(h);
+                    const float u = hu * rh, v = hv * rh;
+                    const float P = hp * gg * fmaf(0.5f, hp, href);
+                    const float c = cs[be], s = sn[be];
+                    Fv[0][qq] = A.cF * hu;
+                    Fv[1][qq] = A.cF * fmaf(hu, u, P);
+                    Fv[2][qq] = A.cF * (hu * v);
+                    const float cGc = A.cG * c;
+                    Gq[0][qq] = cGc * hv;
+                    Gq[1][qq] = cGc * (hv * u);
+                    Gq[2][qq] = cGc * fmaf(hv, v, P);
+                    const float K = s * fmaf(A.twoOmega, c, u * A.invR);
+                    Sv[0][qq] = 0.0f;
+                    Sv[1][qq] = K * hv;
+                    Sv[2][qq] = -(P * s * A.invR) - K * hu;
+                } else {
+#pragma unroll
+                    for (int f = 0; f < 3; ++f) Fv[f][qq] = Gq[f][qq] = Sv[f][qq] = 0.0f;
+                }
+            }
+#pragma unroll
+            for (int f = 0; f < 3; ++f) {
+                put_chunk<OpT>(a2(f, g), Fv[f]);
+                put_chunk<OpT>(a2(f, CN + g), Gq[f]);
+                put_chunk<OpT>(a2(f, 2 * CN + g), Sv[f]);
+            }
+        }
+        if (interior) st_int |= sq;
+    }
+
+    // ---- S3 + S6 on the tensor cores: volume integral and lift
+    fence_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (tid == 0) {
+        const uint32_t b2 = smem_u32(sm + SM::B2);
+        constexpr uint32_t LB2 = N2 * 16;
+        constexpr uint32_t id2 = idesc<Op<OpT>::bf16>(128, N2);
+        for (int t = 0; t < QM; ++t)
+            for (int f = 0; f < 3; ++f)
+                for (int s = 0; s < KC2 / 2; ++s)
+                    mma(tbase + (uint32_t)((t * 3 + f) * N1), sdesc(a0 + (uint32_t)((t * 3 + f) * KC2 + 2 * s) * CH, CH, 128),
+                        sdesc(b2 + 2 * s * LB2, LB2, 128), id2, s > 0);
+        mma_commit(mb);
+    }
+    if (!mbar_wait(mb, 1)) st |= DG_STATUS_TIMEOUT;
+    tc_fence_after();
+    __syncwarp();
+
+    // ---- S7 inverse mass matrix (FP32 on the CUDA cores), S8 combine, store
+    {
+        float Ci[N][N], rho[N];
+#pragma unroll
+        for (int b = 0; b < N; ++b) {
+            rho[b] = __ldg(&A.rows[j].rho[b]);
+#pragma unroll
+            for (int c = 0; c < N; ++c) Ci[b][c] = __ldg(&A.rows[j].Ci[b][c]);
+        }
+        const size_t e0 = (size_t)j * rowlen + i;
+        const float cdt = A.cc * A.dt, adt = A.ca * A.dt;
+#pragma unroll
+        for (int f = 0; f < 3; ++f) {
+            float r[8 * CN];
+#pragma unroll
+            for (int c = 0; c < CN; ++c) tmem_ld8(tl + (uint32_t)((tt * 3 + f) * N1 + 8 * c), r + 8 * c);
+            tmem_wait();
+#pragma unroll
+            for (int c = 0; c < CN; ++c) reg_fence8(r + 8 * c);
+            float kk[NP];
+#pragma unroll
+            for (int b = 0; b < N; ++b)
+#pragma unroll
+                for (int a = 0; a < N; ++a) {
+                    float s = 0.0f;
+#pragma unroll
+                    for (int c = 0; c < N; ++c) s = fmaf(Ci[b][c], r[c * N + a], s);
+                    kk[b * N + a] = s;
+                }
+            if (f == 2) {
+#pragma unroll
+                for (int b = 0; b < N; ++b) kk[b * N] = fmaf(A.P0, rho[b], kk[b * N]);
+            }
+            if (interior) {
+#pragma unroll
+                for (int m = 0; m < NP; ++m) {
+                    const size_t o = e0 + (size_t)(f * NP + m) * A.nlon;
+                    const float kv = kk[m];
+                    if (!isfinite(kv)) st_int |= DG_STATUS_NONFINITE;
+                    if (A.out_rhs) A.out_rhs[o] = kv;
+                    const float inc = A.inc ? __ldg(A.inc + o) : 0.0f;
+                    if (A.inc_out) A.inc_out[o] = fmaf(cdt, kv, A.ci * inc);
+                    const float acc = A.acc_in ? __ldg(A.acc_in + o) : 0.0f;
+                    if (A.acc_out) A.acc_out[o] = fmaf(adt, kv, acc);
+                    if (A.out_base) {
+                        // u^{n+1} = (base + lo) + delta with an error-free two-sum
+                        const float bs = __ldg(A.base + o);
+                        const float lo = A.lo ? __ldg(A.lo + o) : 0.0f;
+                        const float delta = fmaf(cdt, kv, fmaf(A.cd, acc, A.ci * inc));
+                        const float s1 = bs + delta;
+                        const float bp = s1 - bs;
+                        const float err = (bs - (s1 - bp)) + (delta - bp);
+                        const float l1 = lo + err;
+                        const float hi = s1 + l1;
+                        A.out_base[o] = hi;
+                        if (A.out_lo) A.out_lo[o] = l1 - (hi - s1);
+                        if (!isfinite(hi)) st_int |= DG_STATUS_NONFINITE;
+                    }
+                }
+            }
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    if (w == 0) tmem_dealloc(tbase);
+    if (interior) st |= st_int;
+    if (st) atomicOr(A.status, st);
+}
+
+// --------------------------------------------------- contraction check ------
+
+// One GEMM1 of the degree's eval/trace matrix on a 128-row operand, read
+// back from TMEM: the tensor-core building block in isolation.
+template <int N, typename OpT>
+__global__ void __launch_bounds__(128) tc_gemm_check_kernel(const float *__restrict__ a, float *__restrict__ d,
+                                                            const uint4 *__restrict__ gB1, unsigned *status)
+{
+    using GE = TcGeo<N>;
+    constexpr int K1 = GE::K1, K1C = GE::K1C, N1 = GE::N1;
+    constexpr uint32_t SZ_B1 = N1 * K1 * 2, OFF_A = (SZ_B1 + 1023) / 1024 * 1024;
+    extern __shared__ __align__(128) unsigned char sm[];
+    __shared__ __align__(8) uint64_t mbar;
+    __shared__ uint32_t tslot;
+    const int tid = threadIdx.x, w = tid >> 5;
+    if (w == 0) tmem_alloc(smem_u32(&tslot));
+    if (tid == 0) mbar_init(smem_u32(&mbar));
+    for (int c = tid; c < (int)(SZ_B1 / 16); c += 128) reinterpret_cast<uint4 *>(sm)[c] = __ldg(gB1 + c);
+    float v[K1];
+#pragma unroll
+    for (int k = 0; k < K1; ++k) v[k] = a[tid * K1 + k];
+#pragma unroll
+    for (int c = 0; c < K1C; ++c) put_chunk<OpT>(sm + OFF_A + c * CH + tid * 16, v + 8 * c);
+    fence_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tbase = tslot, mb = smem_u32(&mbar);
+    if (tid == 0) {
+        constexpr uint32_t LB1 = N1 * 16;
+        for (int s = 0; s < K1C / 2; ++s)
+            mma(tbase, sdesc(smem_u32(sm + OFF_A) + 2 * s * CH, CH, 128), sdesc(smem_u32(sm) + 2 * s * LB1, LB1, 128),
+                idesc<Op<OpT>::bf16>(128, N1), s > 0);
+        mma_commit(mb);
+    }
+    const bool ok = mbar_wait(mb, 0);
+    tc_fence_after();
+    __syncwarp();
+    const uint32_t tl = tbase + ((uint32_t)(32 * w) << 16);
+#pragma unroll
+    for (int c = 0; c < N1 / 8; ++c) {
+        float r[8];
+        tmem_ld8(tl + 8 * c, r);
+        tmem_wait();
+        reg_fence8(r);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) d[tid * N1 + 8 * c + k] = r[k];
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (w == 0) tmem_dealloc(tbase);
+    if (!ok) atomicOr(status, DG_STATUS_TIMEOUT);
+}
+
+// ------------------------------------------------------------ permutation --
+
+// [lat][lon][el] <-> [lat][el][lon], 32 x 32 tiles through shared memory.
+__global__ void permute_kernel(const float *__restrict__ src, float *__restrict__ dst, int nlon, int el,
+                               int to_lanes)
+{
+    __shared__ float t[32][33];
+    const int j = blockIdx.z;
+    const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;   // r: lon, c: el (in the [lon][el] view)
+    const size_t base = (size_t)j * nlon * el;
+    for (int y = threadIdx.y; y < 32; y += blockDim.y) {
+        if (to_lanes) {
+            const int r = r0 + y, c = c0 + threadIdx.x;
+            if (r < nlon && c < el) t[y][threadIdx.x] = src[base + (size_t)r * el + c];
+        } else {
+            const int c = c0 + y, r = r0 + threadIdx.x;
+            if (r < nlon && c < el) t[threadIdx.x][y] = src[base + (size_t)c * nlon + r];
+        }
+    }
+    __syncthreads();
+    for (int y = threadIdx.y; y < 32; y += blockDim.y) {
+        if (to_lanes) {
+            const int c = c0 + y, r = r0 + threadIdx.x;
+            if (r < nlon && c < el) dst[base + (size_t)c * nlon + r] = t[threadIdx.x][y];
+        } else {
+            const int r = r0 + y, c = c0 + threadIdx.x;
+            if (r < nlon && c < el) dst[base + (size_t)r * el + c] = t[y][threadIdx.x];
+        }
+    }
+}
+
+// ------------------------------------------------------------- host side ----
+
+// Operand B of both GEMMs in the canonical K-major layout: element (r, k) of
+// an R-row operand at byte (k / 8) * R * 16 + r * 16 + (k % 8) * 2.
+template <int N, typename OpT>
+void build_tables(std::vector<uint16_t> &b1, std::vector<uint16_t> &b2)
+{
+    using GE = TcGeo<N>;
+    constexpr int NP = GE::NP, NC = GE::NC, K1 = GE::K1, N1 = GE::N1, N2 = GE::N2, K2 = GE::K2, EW = GE::EW,
+                  CN = GE::CN;
+    double x[DG_MAXN], wq[DG_MAXN];
+    dg_gauss_legendre(N, x, wq);
+    double LV[DG_MAXN][DG_MAXN], LD[DG_MAXN][DG_MAXN], Lm[DG_MAXN], Lp[DG_MAXN];
+    for (int a = 0; a < N; ++a) {
+        for (int q = 0; q < N; ++q) {
+            LV[a][q] = dg_legendre(a, x[q]);
+            LD[a][q] = dg_legendre_deriv(a, x[q]);
+        }
+        Lm[a] = dg_legendre(a, -1.0);
+        Lp[a] = dg_legendre(a, 1.0);
+    }
+    std::vector<double> m1((size_t)N1 * K1, 0.0), m2((size_t)N2 * K2, 0.0);
+    auto B1 = [&](int r, int k) -> double & { return m1[(size_t)r * K1 + k]; };
+    auto B2 = [&](int r, int k) -> double & { return m2[(size_t)r * K2 + k]; };
+    for (int m = 0; m < NP; ++m) {
+        const int a = m % N, b = m / N;
+        for (int q = 0; q < NP; ++q) B1(q, m) = LV[a][q % N] * LV[b][q / N];
+        for (int k = 0; k < N; ++k) {
+            B1(NC + 0 * N + k, m) = LV[a][k] * Lm[b];   // S edge at xi_k
+            B1(NC + 1 * N + k, m) = LV[a][k] * Lp[b];   // N edge
+            B1(NC + 2 * N + k, m) = Lm[a] * LV[b][k];   // W edge at eta_k
+            B1(NC + 3 * N + k, m) = Lp[a] * LV[b][k];   // E edge
+        }
+    }
+    // residual mode m' = (b', a) before C_j^{-1}: volume terms of F, G, S at
+    // the Gauss points, lift of the W, E, S, N edge fluxes
+    for (int r = 0; r < NP; ++r) {
+        const int a = r % N, bp = r / N;
+        for (int q = 0; q < NP; ++q) {
+            const int al = q % N, be = q / N;
+            const double wl_a = wq[al] * LV[a][al], wd_a = wq[al] * LD[a][al];
+            const double wl_b = wq[be] * LV[bp][be], wd_b = wq[be] * LD[bp][be];
+            B2(r, q) = wd_a * wl_b;
+            B2(r, NC + q) = wl_a * wd_b;
+            B2(r, 2 * NC + q) = wl_a * wl_b;
+        }
+        const int E0 = 3 * NC;
+        for (int k = 0; k < N; ++k) {
+            B2(r, E0 + 0 * EW + k) = wq[k] * LV[bp][k] * Lm[a];
+            B2(r, E0 + 1 * EW + k) = -wq[k] * LV[bp][k] * Lp[a];
+            B2(r, E0 + 2 * EW + k) = wq[k] * LV[a][k] * Lm[bp];
+            B2(r, E0 + 3 * EW + k) = -wq[k] * LV[a][k] * Lp[bp];
+        }
+    }
+    (void)CN;
+    auto canon = [](const std::vector<double> &m, int R, int K, std::vector<uint16_t> &out) {
+        out.assign((size_t)R * K, 0);
+        for (int r = 0; r < R; ++r)
+            for (int k = 0; k < K; ++k)
+                out[(size_t)(k / 8) * R * 8 + (size_t)r * 8 + (k % 8)] = Op<OpT>::host_bits((float)m[(size_t)r * K + k]);
+    };
+    canon(m1, N1, K1, b1);
+    canon(m2, N2, K2, b2);
+}
+
+struct TabSet {
+    uint4 *b1 = nullptr, *b2 = nullptr;
+};
+TabSet g_tabs[64][DG_MAXN][2];
+unsigned long long g_attr[DG_MAXN][2];
+unsigned long long g_check_attr[DG_MAXN][2];
+
+template <int N, typename OpT>
+int tables_for(int dev, int op, TabSet &out)
+{
+    TabSet &t = g_tabs[dev][N - 1][op];
+    if (!t.b1) {
+        std::vector<uint16_t> b1, b2;
+        build_tables<N, OpT>(b1, b2);
+        uint4 *d1 = nullptr, *d2 = nullptr;
+        if (cudaMalloc(&d1, b1.size() * 2) != cudaSuccess) return 1;
+        if (cudaMalloc(&d2, b2.size() * 2) != cudaSuccess) {
+            cudaFree(d1);
+            return 1;
+        }
+        if (cudaMemcpy(d1, b1.data(), b1.size() * 2, cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(d2, b2.data(), b2.size() * 2, cudaMemcpyHostToDevice) != cudaSuccess) {
+            cudaFree(d1);
+            cudaFree(d2);
+            return 1;
+        }
+        t.b1 = d1;
+        t.b2 = d2;
+    }
+    out = t;
+    return 0;
+}
+
+// Tables and the shared-memory opt-in of one (degree, operand type) on the
+// current device; allocates and copies, so it must run outside stream capture.
+template <int N, typename OpT>
+int prepare_tc(int op, TabSet &t)
+{
+    constexpr int QM = tc_qm<N>();
+    using SM = TcSmem<N, QM>;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 1;
+    if (tables_for<N, OpT>(dev, op, t)) return 1;
+    if (!(g_attr[N - 1][op] >> dev & 1ull)) {
+        if (cudaFuncSetAttribute(tc_stage_kernel<N, OpT, QM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)SM::BYTES) != cudaSuccess)
+            return 1;
+        g_attr[N - 1][op] |= 1ull << dev;
+    }
+    return 0;
+}
+
+template <int N, typename OpT>
+int launch_tc(int op, const StageArgs<float> &a, cudaStream_t s)
+{
+    constexpr int QM = tc_qm<N>();
+    using SM = TcSmem<N, QM>;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 1;
+    const TabSet t = g_tabs[dev][N - 1][op];
+    if (!t.b1 || !(g_attr[N - 1][op] >> dev & 1ull)) return 1;   // dg_prepare_stage_tc was not called
+    dim3 grid((a.nlon + TC_TW - 1) / TC_TW, (a.nlat + 4 * QM - 1) / (4 * QM));
+    tc_stage_kernel<N, OpT, QM><<<grid, 128 * QM, SM::BYTES, s>>>(a, t.b1, t.b2);
+    return cudaPeekAtLastError() == cudaSuccess ? 0 : 1;
+}
+
+template <int N, typename OpT>
+int check_tc(int op, const float *a, float *d, int *n1, int *k1, cudaStream_t s)
+{
+    using GE = TcGeo<N>;
+    *n1 = GE::N1;
+    *k1 = GE::K1;
+    if (!a || !d) return 0;   // sizes only
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 1;
+    TabSet t;
+    if (tables_for<N, OpT>(dev, op, t)) return 1;
+    constexpr uint32_t bytes = (GE::N1 * GE::K1 * 2 + 1023) / 1024 * 1024 + GE::K1C * CH;
+    if (!(g_check_attr[N - 1][op] >> dev & 1ull)) {
+        if (cudaFuncSetAttribute(tc_gemm_check_kernel<N, OpT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)bytes) != cudaSuccess)
+            return 1;
+        g_check_attr[N - 1][op] |= 1ull << dev;
+    }
+    unsigned *st = nullptr;
+    if (cudaMallocAsync(&st, sizeof(unsigned), s) != cudaSuccess) return 1;
+    cudaMemsetAsync(st, 0, sizeof(unsigned), s);
+    tc_gemm_check_kernel<N, OpT><<<1, 128, bytes, s>>>(a, d, t.b1, st);
+    unsigned h = 0;
+    cudaMemcpyAsync(&h, st, sizeof h, cudaMemcpyDeviceToHost, s);
+    cudaFreeAsync(st, s);
+    if (cudaStreamSynchronize(s) != cudaSuccess) return 1;
+    return h ? 2 : 0;
+}
+
+}  // namespace
+
+int dg_prepare_stage_tc(int n, int op)
+{
+    TabSet t;
+    if (op == 0) {
+        switch (n) {
+        case 1: return prepare_tc<1, __nv_bfloat16>(0, t);
+        case 2: return prepare_tc<2, __nv_bfloat16>(0, t);
+        case 3: return prepare_tc<3, __nv_bfloat16>(0, t);
+        case 4: return prepare_tc<4, __nv_bfloat16>(0, t);
+        case 5: return prepare_tc<5, __nv_bfloat16>(0, t);
+        default: return 1;
+        }
+    }
+    switch (n) {
+    case 1: return prepare_tc<1, __half>(1, t);
+    case 2: return prepare_tc<2, __half>(1, t);
+    case 3: return prepare_tc<3, __half>(1, t);
+    case 4: return prepare_tc<4, __half>(1, t);
+    case 5: return prepare_tc<5, __half>(1, t);
+    default: return 1;
+    }
+}
+
+int dg_launch_stage_tc(int n, int op, const StageArgs<float> &a, void *stream)
+{
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (op == 0) {
+        switch (n) {
+        case 1: return launch_tc<1, __nv_bfloat16>(0, a, s);
+        case 2: return launch_tc<2, __nv_bfloat16>(0, a, s);
+        case 3: return launch_tc<3, __nv_bfloat16>(0, a, s);
+        case 4: return launch_tc<4, __nv_bfloat16>(0, a, s);
+        case 5: return launch_tc<5, __nv_bfloat16>(0, a, s);
+        default: return 1;
+        }
+    }
+    switch (n) {
+    case 1: return launch_tc<1, __half>(1, a, s);
+    case 2: return launch_tc<2, __half>(1, a, s);
+    case 3: return launch_tc<3, __half>(1, a, s);
+    case 4: return launch_tc<4, __half>(1, a, s);
+    case 5: return launch_tc<5, __half>(1, a, s);
+    default: return 1;
+    }
+}
+
+int dg_tc_gemm_check(int n, int op, const float *a, float *d, int *n1, int *k1, void *stream)
+{
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (op == 0) {
+        switch (n) {
+        case 1: return check_tc<1, __nv_bfloat16>(0, a, d, n1, k1, s);
+        case 2: return check_tc<2, __nv_bfloat16>(0, a, d, n1, k1, s);
+        case 3: return check_tc<3, __nv_bfloat16>(0, a, d, n1, k1, s);
+        case 4: return check_tc<4, __nv_bfloat16>(0, a, d, n1, k1, s);
+        case 5: return check_tc<5, __nv_bfloat16>(0, a, d, n1, k1, s);
+        default: return 1;
+        }
+    }
+    switch (n) {
+    case 1: return check_tc<1, __half>(1, a, d, n1, k1, s);
+    case 2: return check_tc<2, __half>(1, a, d, n1, k1, s);
+    case 3: return check_tc<3, __half>(1, a, d, n1, k1, s);
+    case 4: return check_tc<4, __half>(1, a, d, n1, k1, s);
+    case 5: return check_tc<5, __half>(1, a, d, n1, k1, s);
+    default: return 1;
+    }
+}
+
+int dg_launch_permute(const float *src, float *dst, int nlat, int nlon, int el, int to_lanes, void *stream)
+{
+    dim3 grid((el + 31) / 32, (nlon + 31) / 32, nlat), block(32, 8);
+    permute_kernel<<<grid, block, 0, static_cast<cudaStream_t>(stream)>>>(src, dst, nlon, el, to_lanes);
+    return cudaPeekAtLastError() == cudaSuccess ? 0 : 1;
+}

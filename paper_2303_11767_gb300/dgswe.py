@@ -53,6 +53,8 @@ SIGNATURES = {
     "dg_max_dt_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                          ctypes.c_double, ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p]),
     "dg_last_error": (ctypes.c_char_p, [_H]),
+    "dg_tc_check_contraction": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                               ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
     "dg_mlp_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_ulonglong,
                                      ctypes.POINTER(ctypes.c_void_p)]),
     "dg_mlp_destroy": (ctypes.c_int, [_H]),
@@ -120,6 +122,25 @@ def _check(status, h=None):
 
 def set_device(device: int):
     _check(lib().dg_set_device(int(device)))
+
+
+def tc_contraction_shape(degree: int, op: int):
+    """(n1, k1): padded output columns and input modes of the tensor-core
+    eval/trace contraction of this degree (op 0 BF16, 1 FP16)."""
+    n1, k1 = ctypes.c_int(0), ctypes.c_int(0)
+    _check(lib().dg_tc_check_contraction(int(degree), int(op), None, None, ctypes.byref(n1), ctypes.byref(k1)))
+    return n1.value, k1.value
+
+
+def tc_check_contraction(degree: int, op: int, a_dev, out_dev):
+    """D = A * B1 on the tensor cores for device FP32 tensors a [128, k1] and
+    out [128, n1] (torch tensors or raw device pointers)."""
+    n1, k1 = ctypes.c_int(0), ctypes.c_int(0)
+    pa = a_dev.data_ptr() if hasattr(a_dev, "data_ptr") else int(a_dev)
+    po = out_dev.data_ptr() if hasattr(out_dev, "data_ptr") else int(out_dev)
+    _check(lib().dg_tc_check_contraction(int(degree), int(op), ctypes.c_void_p(pa), ctypes.c_void_p(po),
+                                         ctypes.byref(n1), ctypes.byref(k1)))
+    return n1.value, k1.value
 
 
 class Solver:

@@ -221,7 +221,7 @@ def test_nonphysical_and_nonfinite_are_reported(prec):
 
 def test_option_errors():
     with solver(8, 4, 1, "fp64") as s:
-        for key, val, status in [(dgswe.OPT_PRECISION, 2, dgswe.DG_EUNSUPPORTED),
+        for key, val, status in [(dgswe.OPT_PRECISION, 7, dgswe.DG_EINVAL),
                                  (dgswe.OPT_ALPHA_MODE, 1, dgswe.DG_EUNSUPPORTED),
                                  (dgswe.OPT_RK_ORDER, 5, dgswe.DG_EINVAL),
                                  (99, 0, dgswe.DG_EINVAL)]:
