@@ -422,6 +422,19 @@ def main():
         out["fp64_plain"] = {"value": v64, "ms_per_step": sum(t64) / k64, "dtype": "f64", "steps": k64,
                              "speedup_of_value": value / v64}
 
+        # ---- the tensor-core precisions on the same workload (device-timed)
+        for tcp in ("fp32_tc_bf16", "fp32_tc_fp16"):
+            if tcp == args.precision:
+                continue
+            stc = make(tcp)
+            stc.set_state(u0)
+            ktc = max(2, args.steps // 5)
+            ttc = time_device(stc, torch, stream, nsteps, dt, ktc, 1, mass_t, flush)
+            vtc = dof * 3 * nsteps * ktc / (sum(ttc) * 1e-3)
+            out.setdefault("variants", {})[tcp] = {"value": vtc, "ms_per_step": sum(ttc) / ktc,
+                                                   "dtype": DTYPES[tcp], "steps": ktc,
+                                                   "kernel": KERNELS[tcp].format(n=p + 1)}
+
         # ---- end to end through the C-ABI with pinned host buffers
         hin = torch.empty(s.state_len, dtype=torch.float64, pin_memory=True).numpy()
         hout = torch.empty(s.state_len, dtype=torch.float64, pin_memory=True).numpy()
@@ -449,7 +462,7 @@ def main():
                                          f"({3 * leg['nsteps']} stages), FP64, {leg['cores']} threads",
                                "seconds": leg["wall"]}
         errs = {}
-        for prec in sorted({"fp32", "fp64", args.precision}):
+        for prec in sorted({"fp32", "fp64", "fp32_tc_bf16", "fp32_tc_fp16", args.precision}):
             sv = make(prec)
             sv.set_state(leg["u0"])
             sv.step(leg["nsteps"], leg["dt"])

@@ -61,19 +61,16 @@ struct TcGeo {
     static constexpr int TRC = (4 * N + 7) / 8 * 8;   // trace columns read back
 };
 
-// 128-row M tiles per CTA: two for n <= 4 (8 warps), one for n = 5 (its
-// three fields of 64 accumulator columns fill the CTA's share of TMEM).
-template <int N>
-constexpr int tc_qm()
-{
-    return N == 5 ? 1 : 2;
-}
+// Threads per element: warps w and w + 4 share TMEM lane quarter w & 3 (the
+// same 32 elements) and split the element's work, which doubles the warps
+// that hide latency and halves each thread's serial chain.
+constexpr int TC_TPE = 2;
 
-// Shared-memory plan (bytes).  A1 / A1h (GEMM1 operands of the tile and of
-// the halo rows) are dead once GEMM1 has completed, so GEMM2's operand A2
-// reuses the region; the row exchange buffers XN / XS live in node chunks of
-// A2 that are written only after the exchange.
-template <int N, int QM>
+// Shared-memory plan (bytes) of one 4-row tile.  A1 / A1h (GEMM1 operands
+// of the tile and of the halo rows) are dead once GEMM1 has completed, so
+// GEMM2's operand A2 reuses the region; the row exchange buffers XN / XS
+// live in node chunks of A2 that are written only after the exchange.
+template <int N>
 struct TcSmem {
     using GE = TcGeo<N>;
     static constexpr uint32_t B1 = 0;
@@ -81,16 +78,16 @@ struct TcSmem {
     static constexpr uint32_t B2 = (SZ_B1 + 127) / 128 * 128;
     static constexpr uint32_t SZ_B2 = GE::N2 * GE::K2 * 2;
     static constexpr uint32_t A = (B2 + SZ_B2 + 1023) / 1024 * 1024;
-    static constexpr uint32_t SZ_A1 = QM * 3 * GE::K1C * CH;
+    static constexpr uint32_t SZ_A1 = 3 * GE::K1C * CH;
     static constexpr uint32_t SZ_A1H = 3 * GE::K1C * CH;
-    static constexpr uint32_t SZ_A2 = QM * 3 * GE::KC2 * CH;
+    static constexpr uint32_t SZ_A2 = 3 * GE::KC2 * CH;
     static constexpr uint32_t SZ_A = SZ_A1 + SZ_A1H > SZ_A2 ? SZ_A1 + SZ_A1H : SZ_A2;
     static constexpr uint32_t BYTES = A + SZ_A;
-    static constexpr uint32_t XN = A;                   // tile 0, field 0, node chunks
-    static constexpr uint32_t XS = A + GE::KC2 * CH;    // tile 0, field 1, node chunks
-    static constexpr uint32_t SZ_X = 4 * QM * 32 * 3 * N * 4;
+    static constexpr uint32_t XN = A;                   // field 0, node chunks
+    static constexpr uint32_t XS = A + GE::KC2 * CH;    // field 1, node chunks
+    static constexpr uint32_t SZ_X = 4 * 32 * 3 * N * 4;
     static_assert(SZ_X <= 3 * GE::CN * CH, "row exchange exceeds the node chunks");
-    static_assert(QM * 3 * GE::N1 + 48 <= (int)TMEM_COLS, "tensor-memory columns");
+    static_assert(3 * GE::N1 + 48 <= (int)TMEM_COLS, "tensor-memory columns");
     static_assert(BYTES <= 113 * 1024, "two CTAs per SM");
 };
 
@@ -254,26 +251,28 @@ __device__ __forceinline__ void put_chunk(unsigned char *p, const float *v)
 
 // ------------------------------------------------------------ stage kernel --
 
-template <int N, typename OpT, int QM>
-__global__ void __launch_bounds__(128 * QM, 2) tc_stage_kernel(const StageArgs<float> A, const uint4 *__restrict__ gB1,
-                                                            const uint4 *__restrict__ gB2)
+template <int N, typename OpT>
+__global__ void __launch_bounds__(128 * TC_TPE, 2) tc_stage_kernel(const StageArgs<float> A,
+                                                                   const uint4 *__restrict__ gB1,
+                                                                   const uint4 *__restrict__ gB2)
 {
     using GE = TcGeo<N>;
-    using SM = TcSmem<N, QM>;
+    using SM = TcSmem<N>;
     constexpr int NP = GE::NP, CN = GE::CN, NC = GE::NC, K1C = GE::K1C, N1 = GE::N1, N2 = GE::N2, EW = GE::EW,
                   KC2 = GE::KC2, TRC = GE::TRC;
-    constexpr int NT = 128 * QM, ROWS = 4 * QM;
+    constexpr int NT = 128 * TC_TPE;
+    constexpr int PE = 0, PN = 1 % TC_TPE;   // parts doing the lambda / theta faces
     constexpr float MS = Op<OpT>::mom_scale, IMS = 1.0f / Op<OpT>::mom_scale;
     extern __shared__ __align__(128) unsigned char sm[];
     __shared__ __align__(8) uint64_t mbar;
     __shared__ uint32_t tslot;
 
     const int tid = threadIdx.x, w = tid >> 5, l = tid & 31;
-    const int tt = w >> 2, q4 = w & 3;   // M tile of the warp and its TMEM lane quarter
-    const int i0 = blockIdx.x * TC_TW, j0 = blockIdx.y * ROWS;
-    const int Gv = min(TC_TW, A.nlon - i0), Wv = min(ROWS, A.nlat - j0);
-    const bool row_ok = w < Wv;
-    const int j = row_ok ? j0 + w : j0;   // rows past the mesh borrow the first row's tables
+    const int q4 = w & 3, part = w >> 2;   // tile row (= TMEM lane quarter) and share of the element's work
+    const int i0 = blockIdx.x * TC_TW, j0 = blockIdx.y * 4;
+    const int Gv = min(TC_TW, A.nlon - i0), Wv = min(4, A.nlat - j0);
+    const bool row_ok = q4 < Wv;
+    const int j = row_ok ? j0 + q4 : j0;   // rows past the mesh borrow the first row's tables
     const bool lane_ok = l <= Gv + 1;
     const bool interior = row_ok && l >= 1 && l <= Gv;
     const int i = ((i0 + l - 1) % A.nlon + A.nlon) % A.nlon;
@@ -282,43 +281,63 @@ __global__ void __launch_bounds__(128 * QM, 2) tc_stage_kernel(const StageArgs<f
     unsigned st = 0, st_int = 0;   // status of any thread / of interior elements only
     const uint32_t rowoff = (uint32_t)(32 * q4 + l) * 16;
     unsigned char *const opA = sm + SM::A;
+    const RowTab<float> *const RT = A.rows + j;
 
     if (w == 0) tmem_alloc(smem_u32(&tslot));
     if (tid == 0) mbar_init(smem_u32(&mbar));
     for (int c = tid; c < (int)(SM::SZ_B1 / 16); c += NT) reinterpret_cast<uint4 *>(sm + SM::B1)[c] = __ldg(gB1 + c);
     for (int c = tid; c < (int)(SM::SZ_B2 / 16); c += NT) reinterpret_cast<uint4 *>(sm + SM::B2)[c] = __ldg(gB2 + c);
 
-    // ---- S0: stage state u = base + inc of one field of one element -> the
-    //      element's row of a GEMM1 operand (zeros for missing elements)
-    auto stage_field = [&](int jj, bool ok, int f, unsigned char *dst) {
-        float v[8 * K1C];
+    // ---- S0: 8 modes (chunk c) of one field of the stage state u = base + inc
+    //      of one element -> its row of a GEMM1 operand (zeros where missing)
+    auto stage_chunk = [&](int jj, bool ok, int f, int c, unsigned char *dst) {
+        float v[8];
 #pragma unroll
-        for (int m = 0; m < 8 * K1C; ++m) v[m] = 0.0f;
+        for (int k = 0; k < 8; ++k) v[k] = 0.0f;
         if (ok) {
-            const size_t o0 = (size_t)jj * rowlen + (size_t)f * NP * A.nlon + i;
+            const float s = f == 0 ? 1.0f : MS;
+            const size_t o0 = (size_t)jj * rowlen + (size_t)(f * NP + 8 * c) * A.nlon + i;
 #pragma unroll
-            for (int m = 0; m < NP; ++m) v[m] = __ldg(A.base + o0 + (size_t)m * A.nlon);
+            for (int k = 0; k < 8; ++k)
+                if (8 * c + k < NP) v[k] = __ldg(A.base + o0 + (size_t)k * A.nlon);
             if (A.inc) {
 #pragma unroll
-                for (int m = 0; m < NP; ++m) v[m] += __ldg(A.inc + o0 + (size_t)m * A.nlon);
+                for (int k = 0; k < 8; ++k)
+                    if (8 * c + k < NP) v[k] += __ldg(A.inc + o0 + (size_t)k * A.nlon);
             }
-            const float s = f == 0 ? 1.0f : MS;
 #pragma unroll
-            for (int m = 0; m < NP; ++m) v[m] *= s;
+            for (int k = 0; k < 8; ++k) v[k] *= s;
         }
-#pragma unroll
-        for (int c = 0; c < K1C; ++c) put_chunk<OpT>(dst + c * CH, v + 8 * c);
+        put_chunk<OpT>(dst + c * CH, v);
     };
+    // the low parts and the RK4 accumulator are read only by the epilogue:
+    // start moving this thread's share of them into L2 now
+    if (interior && (A.lo || A.acc_in)) {
+        const float *pl = A.lo ? A.lo : A.acc_in;
+        const size_t o0 = (size_t)j * rowlen + i;
+        for (int m = part; m < 3 * NP; m += TC_TPE)
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(pl + o0 + (size_t)m * A.nlon));
+    }
+    // the tile rows: part p stages the chunks c = p, p + TPE, ... (all of its
+    // loads in flight before the first conversion)
 #pragma unroll
-    for (int f = 0; f < 3; ++f)
-        stage_field(j0 + w, row_ok && lane_ok, f, opA + (uint32_t)((tt * 3 + f) * K1C) * CH + rowoff);
-    // halo rows: job = side * 3 + f; side 0 = the row south of the tile
-    // (TMEM quarter 0), side 1 = the row north of it (quarter 3)
-    for (int job = w; job < 6; job += ROWS) {
-        const int side = job / 3, f = job - 3 * side;
-        const int jj = side ? j0 + ROWS : j0 - 1;
+    for (int fc = 0; fc < 3 * K1C; fc += TC_TPE) {
+        if (fc + part < 3 * K1C) {
+            const int f = (fc + part) / K1C, c = (fc + part) - f * K1C;
+            stage_chunk(j0 + q4, row_ok && lane_ok, f, c, opA + (uint32_t)(f * K1C) * CH + rowoff);
+        }
+    }
+    // halo rows: job = (side * 3 + f) * K1C + c; side 0 = the row south of
+    // the tile (TMEM quarter 0), side 1 = the row north of it (quarter 3)
+#pragma unroll
+    for (int job0 = 0; job0 < 6 * K1C; job0 += 4 * TC_TPE) {
+        const int job = job0 + w;
+        if (job >= 6 * K1C) break;
+        const int sf = job / K1C, c = job - sf * K1C;
+        const int side = sf / 3, f = sf - 3 * side;
+        const int jj = side ? j0 + 4 : j0 - 1;
         const bool ok = lane_ok && (side ? jj < A.nlat : jj >= 0);
-        stage_field(ok ? jj : 0, ok, f, opA + SM::SZ_A1 + (uint32_t)(f * K1C) * CH + (uint32_t)((side ? 96 : 0) + l) * 16);
+        stage_chunk(ok ? jj : 0, ok, f, c, opA + SM::SZ_A1 + (uint32_t)(f * K1C) * CH + (uint32_t)((side ? 96 : 0) + l) * 16);
     }
 
     fence_async_smem();
@@ -334,15 +353,13 @@ __global__ void __launch_bounds__(128 * QM, 2) tc_stage_kernel(const StageArgs<f
         const uint32_t b1 = smem_u32(sm + SM::B1);
         constexpr uint32_t LB1 = N1 * 16;
         constexpr uint32_t id1 = idesc<Op<OpT>::bf16>(128, N1), idh = idesc<Op<OpT>::bf16>(128, 16);
-        for (int t = 0; t < QM; ++t)
-            for (int f = 0; f < 3; ++f)
-                for (int s = 0; s < K1C / 2; ++s)
-                    mma(tbase + (uint32_t)((t * 3 + f) * N1), sdesc(a0 + (uint32_t)((t * 3 + f) * K1C + 2 * s) * CH, CH, 128),
-                        sdesc(b1 + 2 * s * LB1, LB1, 128), id1, s > 0);
         for (int f = 0; f < 3; ++f)
             for (int s = 0; s < K1C / 2; ++s)
-                mma(tbase + (uint32_t)(QM * 3 * N1 + 16 * f),
-                    sdesc(a0 + SM::SZ_A1 + (uint32_t)(f * K1C + 2 * s) * CH, CH, 128),
+                mma(tbase + (uint32_t)(f * N1), sdesc(a0 + (uint32_t)(f * K1C + 2 * s) * CH, CH, 128),
+                    sdesc(b1 + 2 * s * LB1, LB1, 128), id1, s > 0);
+        for (int f = 0; f < 3; ++f)
+            for (int s = 0; s < K1C / 2; ++s)
+                mma(tbase + (uint32_t)(3 * N1 + 16 * f), sdesc(a0 + SM::SZ_A1 + (uint32_t)(f * K1C + 2 * s) * CH, CH, 128),
                     sdesc(b1 + NC * 16 + 2 * s * LB1, LB1, 128), idh, s > 0);
         mma_commit(mb);
     }
@@ -351,56 +368,39 @@ __global__ void __launch_bounds__(128 * QM, 2) tc_stage_kernel(const StageArgs<f
     __syncwarp();
 
     const uint32_t tl = tbase + ((uint32_t)(32 * q4) << 16);
+    unsigned char *const a2row = opA + rowoff;
+    auto a2 = [&](int f, int c) { return a2row + (uint32_t)(f * KC2 + c) * CH; };
+    float *XN = reinterpret_cast<float *>(sm + SM::XN);
+    float *XS = reinterpret_cast<float *>(sm + SM::XS);
 
-    // own traces: [0, N) S, [N, 2N) N, [2N, 3N) W, [3N, 4N) E
-    float tr[3][TRC];
+    // own traces of 3 fields, columns [NC + c0, NC + c0 + 2N): (S, N) for
+    // c0 = 0, (W, E) for c0 = 2N; unscaled
+    auto load_traces = [&](int c0, float (*t)[2 * N]) {
+        constexpr int C8 = (2 * N + 7) / 8 + 1;   // 8-column loads covering [c0, c0 + 2N) from an aligned start
+        float raw[3][8 * C8];
+        const int base = (NC + c0) & ~7, sh = (NC + c0) & 7;
 #pragma unroll
-    for (int f = 0; f < 3; ++f)
+        for (int f = 0; f < 3; ++f)
 #pragma unroll
-        for (int c = 0; c < TRC / 8; ++c) tmem_ld8(tl + (uint32_t)((tt * 3 + f) * N1 + NC + 8 * c), &tr[f][8 * c]);
-    tmem_wait();
-#pragma unroll
-    for (int f = 0; f < 3; ++f)
-#pragma unroll
-        for (int c = 0; c < TRC / 8; ++c) reg_fence8(&tr[f][8 * c]);
-#pragma unroll
-    for (int k = 0; k < TRC; ++k) {
-        tr[1][k] *= IMS;
-        tr[2][k] *= IMS;
-    }
-    // halo traces: warp 0 the N trace of the row south of the tile, the last
-    // warp the S trace of the row north of it
-    float halo[3][N];
-    if (w == 0 || w == ROWS - 1) {
-        float hv[3][16];
-#pragma unroll
-        for (int f = 0; f < 3; ++f) {
-            tmem_ld8(tl + (uint32_t)(QM * 3 * N1 + 16 * f), hv[f]);
-            tmem_ld8(tl + (uint32_t)(QM * 3 * N1 + 16 * f + 8), hv[f] + 8);
-        }
+            for (int c = 0; c < C8; ++c) tmem_ld8(tl + (uint32_t)(f * N1 + base + 8 * c), &raw[f][8 * c]);
         tmem_wait();
 #pragma unroll
-        for (int f = 0; f < 3; ++f) {
-            reg_fence8(hv[f]);
-            reg_fence8(hv[f] + 8);
-        }
+        for (int f = 0; f < 3; ++f)
+#pragma unroll
+            for (int c = 0; c < C8; ++c) reg_fence8(&raw[f][8 * c]);
 #pragma unroll
         for (int f = 0; f < 3; ++f)
 #pragma unroll
-            for (int k = 0; k < N; ++k) halo[f][k] = (w == 0 ? hv[f][N + k] : hv[f][k]) * (f == 0 ? 1.0f : IMS);
-    } else {
-#pragma unroll
-        for (int f = 0; f < 3; ++f)
-#pragma unroll
-            for (int k = 0; k < N; ++k) halo[f][k] = 0.0f;
-    }
+            for (int k = 0; k < 2 * N; ++k) t[f][k] = (sh ? raw[f][sh + k] : raw[f][k]) * (f == 0 ? 1.0f : IMS);
+    };
+    (void)TRC;
 
-    unsigned char *const a2row = opA + rowoff;
-    auto a2 = [&](int f, int c) { return a2row + (uint32_t)((tt * 3 + f) * KC2 + c) * CH; };
-
-    // ---- S5 lambda faces: lanes 1..Gv+1 evaluate their W edge (the last one
-    //      is the tile's east boundary); the E edge is the next lane's W edge
-    {
+    // ---- S5 lambda faces (part PE): lanes 1..Gv+1 evaluate their W edge (the
+    //      last one is the tile's east boundary); the E edge is the next
+    //      lane's W edge
+    if (part == PE) {
+        float twe[3][2 * N];   // [0, N) W, [N, 2N) E
+        load_traces(2 * N, twe);
         float efW[3][N], efE[3][N];
         unsigned sw = 0;
 #pragma unroll
@@ -408,8 +408,8 @@ __global__ void __launch_bounds__(128 * QM, 2) tc_stage_kernel(const StageArgs<f
             float L[3], R[3], o[3];
 #pragma unroll
             for (int f = 0; f < 3; ++f) {
-                L[f] = __shfl_up_sync(0xffffffffu, tr[f][3 * N + k], 1);
-                R[f] = tr[f][2 * N + k];
+                L[f] = __shfl_up_sync(0xffffffffu, twe[f][N + k], 1);
+                R[f] = twe[f][k];
             }
             dgk::rusanov_lam(L, R, href, gg, A.cF, o, sw);
 #pragma unroll
@@ -441,104 +441,120 @@ __global__ void __launch_bounds__(128 * QM, 2) tc_stage_kernel(const StageArgs<f
         }
     }
 
-    // ---- S5 theta faces through the row exchange: every element evaluates
-    //      its S edge; its N edge is the S edge of the element above (or,
-    //      for the top row of the tile, is evaluated against the halo row)
-    float *XN = reinterpret_cast<float *>(sm + SM::XN);
-    float *XS = reinterpret_cast<float *>(sm + SM::XS);
+    // ---- S5 theta faces (part PN) through the row exchange: every element
+    //      evaluates its S edge; its N edge is the S edge of the element
+    //      above (for the top row of a full tile: evaluated against the halo)
+    float tsn[3][2 * N];   // [0, N) S, [N, 2N) N
+    float halo[3][N];      // row 0: N trace of the row south; row 3: S trace of the row north
+    if (part == PN) {
+        load_traces(0, tsn);
+        if (q4 == 0 || q4 == 3) {
+            float hv[3][16];
 #pragma unroll
-    for (int f = 0; f < 3; ++f)
+            for (int f = 0; f < 3; ++f) {
+                tmem_ld8(tl + (uint32_t)(3 * N1 + 16 * f), hv[f]);
+                tmem_ld8(tl + (uint32_t)(3 * N1 + 16 * f + 8), hv[f] + 8);
+            }
+            tmem_wait();
 #pragma unroll
-        for (int k = 0; k < N; ++k) XN[((w * 3 + f) * N + k) * 32 + l] = tr[f][N + k];
-    __syncthreads();
-    float efS[3][N], efN[3][N];
-    {
-        float nb[3][N];
+            for (int f = 0; f < 3; ++f) {
+                reg_fence8(hv[f]);
+                reg_fence8(hv[f] + 8);
+            }
+#pragma unroll
+            for (int f = 0; f < 3; ++f)
+#pragma unroll
+                for (int k = 0; k < N; ++k) halo[f][k] = (q4 == 0 ? hv[f][N + k] : hv[f][k]) * (f == 0 ? 1.0f : IMS);
+        }
 #pragma unroll
         for (int f = 0; f < 3; ++f)
 #pragma unroll
-            for (int k = 0; k < N; ++k) nb[f][k] = w > 0 ? XN[(((w - 1) * 3 + f) * N + k) * 32 + l] : halo[f][k];
-        const float cgs = A.cG * __ldg(&A.rows[j].ce_s);
+            for (int k = 0; k < N; ++k) XN[((q4 * 3 + f) * N + k) * 32 + l] = tsn[f][N + k];
+    }
+    __syncthreads();
+    float efS[3][N];
+    if (part == PN) {
+        const float cgs = A.cG * __ldg(&RT->ce_s);
         unsigned ss = 0;
 #pragma unroll
         for (int k = 0; k < N; ++k) {
             float Sq[3], Nq[3], o[3];
 #pragma unroll
             for (int f = 0; f < 3; ++f) {
-                Sq[f] = nb[f][k];
-                Nq[f] = tr[f][k];
+                Sq[f] = q4 > 0 ? XN[(((q4 - 1) * 3 + f) * N + k) * 32 + l] : halo[f][k];
+                Nq[f] = tsn[f][k];
             }
             dgk::rusanov_th(Sq, Nq, href, gg, cgs, o, ss);
 #pragma unroll
-            for (int f = 0; f < 3; ++f) efS[f][k] = j0 + w > 0 ? o[f] : 0.0f;   // pole edge: zero flux
+            for (int f = 0; f < 3; ++f) efS[f][k] = j0 + q4 > 0 ? o[f] : 0.0f;   // pole edge: zero flux
         }
-        if (interior && j0 + w > 0) st_int |= ss;
+        if (interior && j0 + q4 > 0) st_int |= ss;
+#pragma unroll
+        for (int f = 0; f < 3; ++f)
+#pragma unroll
+            for (int k = 0; k < N; ++k) XS[((q4 * 3 + f) * N + k) * 32 + l] = efS[f][k];
     }
-#pragma unroll
-    for (int f = 0; f < 3; ++f)
-#pragma unroll
-        for (int k = 0; k < N; ++k) XS[((w * 3 + f) * N + k) * 32 + l] = efS[f][k];
     __syncthreads();
-    if (w + 1 < Wv) {
+    float efN[3][N];
+    if (part == PN) {
+        if (q4 + 1 < Wv) {
 #pragma unroll
-        for (int f = 0; f < 3; ++f)
+            for (int f = 0; f < 3; ++f)
 #pragma unroll
-            for (int k = 0; k < N; ++k) efN[f][k] = XS[(((w + 1) * 3 + f) * N + k) * 32 + l];
-    } else if (j0 + w + 1 >= A.nlat) {
+                for (int k = 0; k < N; ++k) efN[f][k] = XS[(((q4 + 1) * 3 + f) * N + k) * 32 + l];
+        } else if (j0 + q4 + 1 >= A.nlat) {
 #pragma unroll
-        for (int f = 0; f < 3; ++f)
+            for (int f = 0; f < 3; ++f)
 #pragma unroll
-            for (int k = 0; k < N; ++k) efN[f][k] = 0.0f;   // pole edge (or a row past the mesh)
-    } else {   // the last warp of a full tile: its N neighbours are the halo row
-        const float cgn = A.cG * __ldg(&A.rows[j].ce_n);
-        unsigned sn = 0;
+                for (int k = 0; k < N; ++k) efN[f][k] = 0.0f;   // pole edge (or a row past the mesh)
+        } else {   // the top row of a full tile: its N neighbours are the halo row
+            const float cgn = A.cG * __ldg(&RT->ce_n);
+            unsigned sn = 0;
 #pragma unroll
-        for (int k = 0; k < N; ++k) {
-            float Sq[3], Nq[3], o[3];
+            for (int k = 0; k < N; ++k) {
+                float Sq[3], Nq[3], o[3];
 #pragma unroll
-            for (int f = 0; f < 3; ++f) {
-                Sq[f] = tr[f][N + k];
-                Nq[f] = halo[f][k];
+                for (int f = 0; f < 3; ++f) {
+                    Sq[f] = tsn[f][N + k];
+                    Nq[f] = halo[f][k];
+                }
+                dgk::rusanov_th(Sq, Nq, href, gg, cgn, o, sn);
+#pragma unroll
+                for (int f = 0; f < 3; ++f) efN[f][k] = o[f];
             }
-            dgk::rusanov_th(Sq, Nq, href, gg, cgn, o, sn);
-#pragma unroll
-            for (int f = 0; f < 3; ++f) efN[f][k] = o[f];
+            if (interior) st_int |= sn;
         }
-        if (interior) st_int |= sn;
     }
     __syncthreads();   // the exchange buffers turn back into operand chunks
+    if (part == PN) {
 #pragma unroll
-    for (int f = 0; f < 3; ++f) {
-        float c0[8], c1[8];
+        for (int f = 0; f < 3; ++f) {
+            float c0[8], c1[8];
 #pragma unroll
-        for (int k = 0; k < 8; ++k) c0[k] = c1[k] = 0.0f;
+            for (int k = 0; k < 8; ++k) c0[k] = c1[k] = 0.0f;
 #pragma unroll
-        for (int k = 0; k < N; ++k) {
-            c0[k] = efS[f][k];
-            if (EW == 4) c0[4 + k] = efN[f][k];
-            else c1[k] = efN[f][k];
-        }
-        if (EW == 4) put_chunk<OpT>(a2(f, 3 * CN + 1), c0);
-        else {
-            put_chunk<OpT>(a2(f, 3 * CN + 2), c0);
-            put_chunk<OpT>(a2(f, 3 * CN + 3), c1);
+            for (int k = 0; k < N; ++k) {
+                c0[k] = efS[f][k];
+                if (EW == 4) c0[4 + k] = efN[f][k];
+                else c1[k] = efN[f][k];
+            }
+            if (EW == 4) put_chunk<OpT>(a2(f, 3 * CN + 1), c0);
+            else {
+                put_chunk<OpT>(a2(f, 3 * CN + 2), c0);
+                put_chunk<OpT>(a2(f, 3 * CN + 3), c1);
+            }
         }
     }
 
-    // ---- S2 pointwise fluxes and sources at the Gauss points, 8 at a time
+    // ---- S2 pointwise fluxes and sources at the Gauss points, 8 at a time;
+    //      part p takes the chunks g = p, p + TPE, ...
     {
-        float cs[N], sn[N];
-#pragma unroll
-        for (int b = 0; b < N; ++b) {
-            cs[b] = __ldg(&A.rows[j].cosn[b]);
-            sn[b] = __ldg(&A.rows[j].sinn[b]);
-        }
         unsigned sq = 0;
-#pragma unroll
-        for (int g = 0; g < CN; ++g) {
+#pragma unroll 1
+        for (int g = part; g < CN; g += TC_TPE) {
             float x[3][8];
 #pragma unroll
-            for (int f = 0; f < 3; ++f) tmem_ld8(tl + (uint32_t)((tt * 3 + f) * N1 + 8 * g), x[f]);
+            for (int f = 0; f < 3; ++f) tmem_ld8(tl + (uint32_t)(f * N1 + 8 * g), x[f]);
             tmem_wait();
 #pragma unroll
             for (int f = 0; f < 3; ++f) reg_fence8(x[f]);
@@ -554,7 +570,7 @@ __global__ void __launch_bounds__(128 * QM, 2) tc_stage_kernel(const StageArgs<f
                     const float rh = dgk::rcp(h);
                     const float u = hu * rh, v = hv * rh;
                     const float P = hp * gg * fmaf(0.5f, hp, href);
-                    const float c = cs[be], s = sn[be];
+                    const float c = __ldg(&RT->cosn[be]), sn = __ldg(&RT->sinn[be]);
                     Fv[0][qq] = A.cF * hu;
                     Fv[1][qq] = A.cF * fmaf(hu, u, P);
                     Fv[2][qq] = A.cF * (hu * v);
@@ -562,10 +578,10 @@ __global__ void __launch_bounds__(128 * QM, 2) tc_stage_kernel(const StageArgs<f
                     Gq[0][qq] = cGc * hv;
                     Gq[1][qq] = cGc * (hv * u);
                     Gq[2][qq] = cGc * fmaf(hv, v, P);
-                    const float K = s * fmaf(A.twoOmega, c, u * A.invR);
+                    const float K = sn * fmaf(A.twoOmega, c, u * A.invR);
                     Sv[0][qq] = 0.0f;
                     Sv[1][qq] = K * hv;
-                    Sv[2][qq] = -(P * s * A.invR) - K * hu;
+                    Sv[2][qq] = -(P * sn * A.invR) - K * hu;
                 } else {
 #pragma unroll
                     for (int f = 0; f < 3; ++f) Fv[f][qq] = Gq[f][qq] = Sv[f][qq] = 0.0f;
@@ -590,74 +606,86 @@ __global__ void __launch_bounds__(128 * QM, 2) tc_stage_kernel(const StageArgs<f
         const uint32_t b2 = smem_u32(sm + SM::B2);
         constexpr uint32_t LB2 = N2 * 16;
         constexpr uint32_t id2 = idesc<Op<OpT>::bf16>(128, N2);
-        for (int t = 0; t < QM; ++t)
-            for (int f = 0; f < 3; ++f)
-                for (int s = 0; s < KC2 / 2; ++s)
-                    mma(tbase + (uint32_t)((t * 3 + f) * N1), sdesc(a0 + (uint32_t)((t * 3 + f) * KC2 + 2 * s) * CH, CH, 128),
-                        sdesc(b2 + 2 * s * LB2, LB2, 128), id2, s > 0);
+        for (int f = 0; f < 3; ++f)
+            for (int s = 0; s < KC2 / 2; ++s)
+                mma(tbase + (uint32_t)(f * N1), sdesc(a0 + (uint32_t)(f * KC2 + 2 * s) * CH, CH, 128),
+                    sdesc(b2 + 2 * s * LB2, LB2, 128), id2, s > 0);
         mma_commit(mb);
     }
     if (!mbar_wait(mb, 1)) st |= DG_STATUS_TIMEOUT;
     tc_fence_after();
     __syncwarp();
 
-    // ---- S7 inverse mass matrix (FP32 on the CUDA cores), S8 combine, store
+    // ---- S7 inverse mass matrix (FP32 on the CUDA cores), S8 combine, store.
+    //      Part p owns the mode rows b of field f with (f N + b) mod TPE = p;
+    //      per field, all of its global inputs are requested before the first
+    //      is used.
     {
-        float Ci[N][N], rho[N];
-#pragma unroll
-        for (int b = 0; b < N; ++b) {
-            rho[b] = __ldg(&A.rows[j].rho[b]);
-#pragma unroll
-            for (int c = 0; c < N; ++c) Ci[b][c] = __ldg(&A.rows[j].Ci[b][c]);
-        }
+        constexpr int RPF = (N + TC_TPE - 1) / TC_TPE;   // rows per field and part, at most
         const size_t e0 = (size_t)j * rowlen + i;
         const float cdt = A.cc * A.dt, adt = A.ca * A.dt;
-#pragma unroll
+        const bool fin = A.out_base != nullptr;
+#pragma unroll 1
         for (int f = 0; f < 3; ++f) {
+            const int b0 = ((part - f * N) % TC_TPE + TC_TPE) % TC_TPE;
+            float vinc[RPF][N], vacc[RPF][N], vbase[RPF][N], vlo[RPF][N];
+#pragma unroll
+            for (int rr = 0; rr < RPF; ++rr) {
+                const int b = b0 + rr * TC_TPE;
+                const bool ok = interior && b < N;
+                const size_t ob = e0 + (size_t)(f * NP + b * N) * A.nlon;
+#pragma unroll
+                for (int a = 0; a < N; ++a) {
+                    const size_t o = ob + (size_t)(a * A.nlon);
+                    vinc[rr][a] = ok && A.inc ? __ldg(A.inc + o) : 0.0f;
+                    vacc[rr][a] = ok && A.acc_in ? __ldg(A.acc_in + o) : 0.0f;
+                    vbase[rr][a] = ok && fin ? __ldg(A.base + o) : 0.0f;
+                    vlo[rr][a] = ok && fin && A.lo ? __ldg(A.lo + o) : 0.0f;
+                }
+            }
             float r[8 * CN];
 #pragma unroll
-            for (int c = 0; c < CN; ++c) tmem_ld8(tl + (uint32_t)((tt * 3 + f) * N1 + 8 * c), r + 8 * c);
+            for (int c = 0; c < CN; ++c) tmem_ld8(tl + (uint32_t)(f * N1 + 8 * c), r + 8 * c);
             tmem_wait();
 #pragma unroll
             for (int c = 0; c < CN; ++c) reg_fence8(r + 8 * c);
-            float kk[NP];
 #pragma unroll
-            for (int b = 0; b < N; ++b)
+            for (int rr = 0; rr < RPF; ++rr) {
+                const int b = b0 + rr * TC_TPE;
+                if (b >= N) break;
+                float kk[N];
 #pragma unroll
-                for (int a = 0; a < N; ++a) {
-                    float s = 0.0f;
+                for (int a = 0; a < N; ++a) kk[a] = 0.0f;
 #pragma unroll
-                    for (int c = 0; c < N; ++c) s = fmaf(Ci[b][c], r[c * N + a], s);
-                    kk[b * N + a] = s;
+                for (int c = 0; c < N; ++c) {
+                    const float cic = __ldg(&RT->Ci[b][c]);
+#pragma unroll
+                    for (int a = 0; a < N; ++a) kk[a] = fmaf(cic, r[c * N + a], kk[a]);
                 }
-            if (f == 2) {
+                if (f == 2) kk[0] = fmaf(A.P0, __ldg(&RT->rho[b]), kk[0]);
+                if (interior) {
+                    const size_t ob = e0 + (size_t)(f * NP + b * N) * A.nlon;
 #pragma unroll
-                for (int b = 0; b < N; ++b) kk[b * N] = fmaf(A.P0, rho[b], kk[b * N]);
-            }
-            if (interior) {
-#pragma unroll
-                for (int m = 0; m < NP; ++m) {
-                    const size_t o = e0 + (size_t)(f * NP + m) * A.nlon;
-                    const float kv = kk[m];
-                    if (!isfinite(kv)) st_int |= DG_STATUS_NONFINITE;
-                    if (A.out_rhs) A.out_rhs[o] = kv;
-                    const float inc = A.inc ? __ldg(A.inc + o) : 0.0f;
-                    if (A.inc_out) A.inc_out[o] = fmaf(cdt, kv, A.ci * inc);
-                    const float acc = A.acc_in ? __ldg(A.acc_in + o) : 0.0f;
-                    if (A.acc_out) A.acc_out[o] = fmaf(adt, kv, acc);
-                    if (A.out_base) {
-                        // u^{n+1} = (base + lo) + delta with an error-free two-sum
-                        const float bs = __ldg(A.base + o);
-                        const float lo = A.lo ? __ldg(A.lo + o) : 0.0f;
-                        const float delta = fmaf(cdt, kv, fmaf(A.cd, acc, A.ci * inc));
-                        const float s1 = bs + delta;
-                        const float bp = s1 - bs;
-                        const float err = (bs - (s1 - bp)) + (delta - bp);
-                        const float l1 = lo + err;
-                        const float hi = s1 + l1;
-                        A.out_base[o] = hi;
-                        if (A.out_lo) A.out_lo[o] = l1 - (hi - s1);
-                        if (!isfinite(hi)) st_int |= DG_STATUS_NONFINITE;
+                    for (int a = 0; a < N; ++a) {
+                        const size_t o = ob + (size_t)(a * A.nlon);
+                        const float kv = kk[a], inc = vinc[rr][a], acc = vacc[rr][a];
+                        if (!isfinite(kv)) st_int |= DG_STATUS_NONFINITE;
+                        if (A.out_rhs) A.out_rhs[o] = kv;
+                        if (A.inc_out) A.inc_out[o] = fmaf(cdt, kv, A.ci * inc);
+                        if (A.acc_out) A.acc_out[o] = fmaf(adt, kv, acc);
+                        if (fin) {
+                            // u^{n+1} = (base + lo) + delta with an error-free two-sum
+                            const float bs = vbase[rr][a], lo = vlo[rr][a];
+                            const float delta = fmaf(cdt, kv, fmaf(A.cd, acc, A.ci * inc));
+                            const float s1 = bs + delta;
+                            const float bp = s1 - bs;
+                            const float err = (bs - (s1 - bp)) + (delta - bp);
+                            const float l1 = lo + err;
+                            const float hi = s1 + l1;
+                            A.out_base[o] = hi;
+                            if (A.out_lo) A.out_lo[o] = l1 - (hi - s1);
+                            if (!isfinite(hi)) st_int |= DG_STATUS_NONFINITE;
+                        }
                     }
                 }
             }
@@ -859,13 +887,12 @@ int tables_for(int dev, int op, TabSet &out)
 template <int N, typename OpT>
 int prepare_tc(int op, TabSet &t)
 {
-    constexpr int QM = tc_qm<N>();
-    using SM = TcSmem<N, QM>;
+    using SM = TcSmem<N>;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 1;
     if (tables_for<N, OpT>(dev, op, t)) return 1;
     if (!(g_attr[N - 1][op] >> dev & 1ull)) {
-        if (cudaFuncSetAttribute(tc_stage_kernel<N, OpT, QM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        if (cudaFuncSetAttribute(tc_stage_kernel<N, OpT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)SM::BYTES) != cudaSuccess)
             return 1;
         g_attr[N - 1][op] |= 1ull << dev;
@@ -876,14 +903,13 @@ int prepare_tc(int op, TabSet &t)
 template <int N, typename OpT>
 int launch_tc(int op, const StageArgs<float> &a, cudaStream_t s)
 {
-    constexpr int QM = tc_qm<N>();
-    using SM = TcSmem<N, QM>;
+    using SM = TcSmem<N>;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 1;
     const TabSet t = g_tabs[dev][N - 1][op];
     if (!t.b1 || !(g_attr[N - 1][op] >> dev & 1ull)) return 1;   // dg_prepare_stage_tc was not called
-    dim3 grid((a.nlon + TC_TW - 1) / TC_TW, (a.nlat + 4 * QM - 1) / (4 * QM));
-    tc_stage_kernel<N, OpT, QM><<<grid, 128 * QM, SM::BYTES, s>>>(a, t.b1, t.b2);
+    dim3 grid((a.nlon + TC_TW - 1) / TC_TW, (a.nlat + 3) / 4);
+    tc_stage_kernel<N, OpT><<<grid, 128 * TC_TPE, SM::BYTES, s>>>(a, t.b1, t.b2);
     return cudaPeekAtLastError() == cudaSuccess ? 0 : 1;
 }
 
