@@ -555,7 +555,9 @@ template <typename T, int N, int W>
 __global__ void __launch_bounds__(32 * W) stage_kernel(const StageArgs<T> A)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    pdl_wait();
     stage_tile<T, N, W>(A, blockIdx.x, blockIdx.y, smem_raw);
+    pdl_launch_dependents();
 }
 
 template <typename T, int N, int W>
@@ -582,7 +584,7 @@ int launch_stage_n(const StageArgs<T> &a, cudaStream_t s)
         attr_set |= 1ull << dev;
     }
     dim3 grid((a.nlon + GE::G - 1) / GE::G, (a.nlat + W - 1) / W);
-    stage_kernel<T, N, W><<<grid, 32 * W, smem, s>>>(a);
+    if (launch_pdl(stage_kernel<T, N, W>, grid, dim3(32 * W), smem, s, a) != cudaSuccess) return 1;
     return cudaPeekAtLastError() == cudaSuccess ? 0 : 1;
 }
 

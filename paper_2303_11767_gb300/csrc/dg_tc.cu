@@ -283,10 +283,13 @@ __global__ void __launch_bounds__(128 * TC_TPE, 2) tc_stage_kernel(const StageAr
     unsigned char *const opA = sm + SM::A;
     const RowTab<float> *const RT = A.rows + j;
 
+    // prologue (independent of the previous kernel's results): tensor
+    // memory, the completion barrier, the two basis operands
     if (w == 0) tmem_alloc(smem_u32(&tslot));
     if (tid == 0) mbar_init(smem_u32(&mbar));
     for (int c = tid; c < (int)(SM::SZ_B1 / 16); c += NT) reinterpret_cast<uint4 *>(sm + SM::B1)[c] = __ldg(gB1 + c);
     for (int c = tid; c < (int)(SM::SZ_B2 / 16); c += NT) reinterpret_cast<uint4 *>(sm + SM::B2)[c] = __ldg(gB2 + c);
+    dgk::pdl_wait();
 
     // ---- S0: 8 modes (chunk c) of one field of the stage state u = base + inc
     //      of one element -> its row of a GEMM1 operand (zeros where missing)
@@ -692,6 +695,7 @@ __global__ void __launch_bounds__(128 * TC_TPE, 2) tc_stage_kernel(const StageAr
         }
     }
 
+    dgk::pdl_launch_dependents();
     tc_fence_before();
     __syncthreads();
     if (w == 0) tmem_dealloc(tbase);
@@ -909,7 +913,9 @@ int launch_tc(int op, const StageArgs<float> &a, cudaStream_t s)
     const TabSet t = g_tabs[dev][N - 1][op];
     if (!t.b1 || !(g_attr[N - 1][op] >> dev & 1ull)) return 1;   // dg_prepare_stage_tc was not called
     dim3 grid((a.nlon + TC_TW - 1) / TC_TW, (a.nlat + 3) / 4);
-    tc_stage_kernel<N, OpT><<<grid, 128 * TC_TPE, SM::BYTES, s>>>(a, t.b1, t.b2);
+    if (dgk::launch_pdl(tc_stage_kernel<N, OpT>, grid, dim3(128 * TC_TPE), SM::BYTES, s, a,
+                        (const uint4 *)t.b1, (const uint4 *)t.b2) != cudaSuccess)
+        return 1;
     return cudaPeekAtLastError() == cudaSuccess ? 0 : 1;
 }
 
