@@ -13,6 +13,8 @@ stays within K dt C u |S| of the oracle's, plus the FP32 state tolerance.
 The contraction itself (exact products of rounded operands, FP32 sums of at
 most 32 terms) matches an FP64 product of the rounded operands to 1e-5.
 """
+import os
+
 import numpy as np
 import pytest
 from numpy.polynomial import legendre as npleg
@@ -211,3 +213,37 @@ def test_first_use_is_a_captured_step():
     r = subprocess.run([sys.executable, "-c", code], cwd=root, capture_output=True, text=True, timeout=300)
     assert r.returncode == 0, r.stderr
     assert r.stdout.split() == ["ok", "48"]
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp32_tc_bf16", "fp32_tc_fp16"])
+def test_precision_config_360x180_p4_500_steps(prec):
+    """The precision configuration: 360x180, degree 4, 500 SSP-RK3 steps at
+    CFL 0.1, per-field relative L2 and max error against the FP64 oracle."""
+    nlon, nlat, p, seed, nsteps = 360, 180, 4, 3, 500
+    key = ("run500", nlon, nlat, p, seed)
+    o, u = case(nlon, nlat, p, seed)
+    if key not in _cache:
+        o.set_threads(os.cpu_count() or 1)
+        dt = o.max_dt(u, 0.1)
+        _cache[key] = (dt, o.step(u, nsteps, dt, 3), o.rhs_magnitude(u))
+    dt, want, S = _cache[key]
+    with dgswe.Solver(nlon, nlat, p, R, G, OMEGA, precision=prec) as s:
+        s.set_option(dgswe.OPT_STEPS_PER_GRAPH, 100)
+        s.set_state(u)
+        m0 = s.total_mass()
+        s.step(nsteps, dt)
+        got = s.get_state()
+        m1 = s.total_mass()
+    errs = []
+    for f in range(3):
+        d = got[..., f, :] - want[..., f, :]
+        errs.append((np.linalg.norm(d) / np.linalg.norm(want[..., f, :]), np.abs(d).max() / np.abs(want[..., f, :]).max()))
+    print(f"\n{prec} 360x180 p=4, 500 steps: rel L2 / max per field (h, hu, hv):",
+          " ".join("%.2e/%.2e" % e for e in errs), "mass drift %.1e" % (m1 / m0 - 1))
+    tol = 1e-5 if prec == "fp32" else C * OPS[prec][1]
+    for f in range(3):
+        d = np.abs(got[..., f, :] - want[..., f, :]).max()
+        bound = (0.0 if prec == "fp32" else nsteps * dt * tol * S[..., f, :].max()) + \
+            1e-5 * np.abs(want[..., f, :]).max()
+        assert d <= bound, (f, d, bound)
+    assert abs(m1 / m0 - 1) < 1e-9
