@@ -72,8 +72,12 @@ typedef enum {
                                     default 3 */
     DG_OPT_CHECK_FINITE = 3,     /* 0/1, default 1: dg_step and dg_rhs report
                                     DG_ENONFINITE / DG_ENONPHYSICAL */
-    DG_OPT_ALPHA_MODE = 4,       /* 0 local Rusanov alpha (default); 1 global
-                                    (returns DG_EUNSUPPORTED) */
+    DG_OPT_ALPHA_MODE = 4,       /* 0: local Rusanov alpha, the larger one-sided
+                                    speed of each face point (default); 1: global,
+                                    every face uses the maxima of |u| + sqrt(gh)
+                                    (lambda faces) and |v| + sqrt(gh) (theta faces)
+                                    over all Gauss points of the stage input,
+                                    computed by one extra kernel per stage */
     DG_OPT_STREAM = 5,           /* cudaStream_t cast to long long; 0 = the
                                     library's own non-blocking stream */
     DG_OPT_STEPS_PER_GRAPH = 6,  /* time steps captured per CUDA graph, 1..1024,

@@ -36,6 +36,8 @@ def lib():
                                                     ctypes.c_double, ctypes.c_double, ctypes.c_int]
         L.oracle_destroy.argtypes = [ctypes.c_void_p]
         L.oracle_set_threads.argtypes = [ctypes.c_void_p, ctypes.c_int]
+        L.oracle_set_alpha_mode.argtypes = [ctypes.c_void_p, ctypes.c_int]
+        L.oracle_set_alpha_mode.restype = ctypes.c_int
         L.oracle_state_len.restype = ctypes.c_size_t
         L.oracle_state_len.argtypes = [ctypes.c_void_p]
         L.oracle_nm.restype = ctypes.c_int
@@ -145,6 +147,11 @@ class Oracle:
 
     def set_threads(self, n: int):
         lib().oracle_set_threads(self._h, int(n))
+
+    def set_alpha_mode(self, mode: int):
+        """0: local Rusanov alpha (default); 1: the global speeds of the stage input."""
+        if lib().oracle_set_alpha_mode(self._h, int(mode)) != 0:
+            raise ValueError(f"alpha mode {mode} not available for this oracle")
 
     def _in(self, u):
         u = np.ascontiguousarray(u, dtype=np.float64).reshape(-1)

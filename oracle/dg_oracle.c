@@ -34,6 +34,10 @@
  *     projections and norms; local Rusanov alpha = max over both sides of the
  *     largest eigenvalue of dF/dU (resp. dG/dU); the whole numerical flux is zero
  *     on the pole edges; integrals in (lambda, theta) without R^2.
+ *   global Rusanov mode (optional): the one-sided speeds |u| + sqrt(gh) and
+ *     |v| + sqrt(gh) of every face are replaced by their maxima over all Gauss
+ *     points of the stage input, inside the same eigenvalue (so the lambda
+ *     faces keep their 1/(R cos theta) and the theta faces their 1/R).
  */
 #include <math.h>
 #include <stdint.h>
@@ -60,6 +64,7 @@ typedef struct {
     double R, g, omega;
     double bx, by;     /* advection velocity (planar advection only) */
     int alpha_speed;   /* planar advection: 1 -> alpha = |beta|, 0 -> |beta . n| */
+    int alpha_global;  /* sphere: 1 -> the wave speeds of every face are the global maxima */
     double x0, y0, dx, dy;
     double *xg, *wg;   /* n-point Gauss-Legendre rule on [-1, 1] */
     double *xm, *wm;   /* nm-point rule */
@@ -396,14 +401,21 @@ static double max_eigenvalue(const oracle_ctx *c, const double *q, double y, int
  * with U = w(y) q the conserved variable and alpha the larger of the two
  * one-sided eigenvalue estimates.  Returns 0 if a state is non-physical. */
 static int numerical_flux(const oracle_ctx *c, const double *qown, const double *qnb, double y,
-                          int nx, int ny, double *fn)
+                          int nx, int ny, const double *gspeed, double *fn)
 {
     double Fo[3], Go[3], So[3], Fb[3], Gb[3], Sb[3];
     if (!physical_flux(c, qown, y, Fo, Go, So)) return 0;
     if (!physical_flux(c, qnb, y, Fb, Gb, Sb)) return 0;
-    double a1 = max_eigenvalue(c, qown, y, nx, ny);
-    double a2 = max_eigenvalue(c, qnb, y, nx, ny);
-    double alpha = a1 > a2 ? a1 : a2;
+    double alpha;
+    if (gspeed) {
+        /* global mode: |u| + c (lambda faces) or |v| + c (theta faces) replaced
+         * by its maximum over the whole stage input, in the same eigenvalue */
+        alpha = nx != 0 ? gspeed[0] / (c->R * cos(y)) : gspeed[1] / c->R;
+    } else {
+        double a1 = max_eigenvalue(c, qown, y, nx, ny);
+        double a2 = max_eigenvalue(c, qnb, y, nx, ny);
+        alpha = a1 > a2 ? a1 : a2;
+    }
     double wy = metric_weight(c, y);
     for (int f = 0; f < c->nf; ++f) {
         double fo = Fo[f] * nx + Go[f] * ny;
@@ -437,11 +449,48 @@ static void eval_point(const oracle_ctx *c, const double *modes, const double *p
  *     = int S phi
  * assembled in (x, y) = (lambda, theta) coordinates and multiplied by the
  * inverse element mass matrix of Eq. (ode).  out: nf * nphi values. */
-static int rhs_element_impl(const oracle_ctx *c, const double *u, int jy, int ix, double *out, int mag);
+static int rhs_element_impl(const oracle_ctx *c, const double *u, int jy, int ix, double *out, int mag,
+                            const double *gspeed);
 
+/* Global wave speeds of a state for the global Rusanov mode: the maxima of
+ * |u| + sqrt(g h) and |v| + sqrt(g h) over all elements and Gauss points. */
+static int global_speeds(const oracle_ctx *c, const double *u, double *gs)
+{
+    double q[3];
+    gs[0] = gs[1] = 0.0;
+    for (int jy = 0; jy < c->ny; ++jy)
+        for (int ix = 0; ix < c->nx; ++ix)
+            for (int qi = 0; qi < c->n * c->n; ++qi) {
+                eval_point(c, elem_modes(c, u, jy, ix), c->phiv + qi * c->nphi, q);
+                if (!(q[0] > 0.0)) return ORACLE_ENONPHYSICAL;
+                double cs = sqrt(c->g * q[0]);
+                double su = fabs(q[1] / q[0]) + cs, sv = fabs(q[2] / q[0]) + cs;
+                if (su > gs[0]) gs[0] = su;
+                if (sv > gs[1]) gs[1] = sv;
+            }
+    return ORACLE_OK;
+}
+
+/* Global Rusanov mode on the sphere: 1 -> every face uses the global speeds
+ * of the stage input, 0 (default) -> the larger of the two one-sided ones. */
+int oracle_set_alpha_mode(oracle_ctx *c, int mode)
+{
+    if (mode != 0 && mode != 1) return ORACLE_EINVAL;
+    if (mode == 1 && c->physics != PHYS_SPHERE_SWE) return ORACLE_EINVAL;
+    c->alpha_global = mode;
+    return ORACLE_OK;
+}
+
+/* One element's tendency; in the global Rusanov mode the global speeds are
+ * taken over the whole state u first (a full pass per call). */
 int oracle_rhs_element(const oracle_ctx *c, const double *u, int jy, int ix, double *out)
 {
-    return rhs_element_impl(c, u, jy, ix, out, 0);
+    double gs[2];
+    if (c->alpha_global) {
+        int st = global_speeds(c, u, gs);
+        if (st) return st;
+    }
+    return rhs_element_impl(c, u, jy, ix, out, 0, c->alpha_global ? gs : NULL);
 }
 
 /* Magnitude bound of the tendency of element (jy, ix): the same assembly with
@@ -451,10 +500,16 @@ int oracle_rhs_element(const oracle_ctx *c, const double *u, int jy, int ix, dou
  * this bound, so it is the scale that tendency tolerances are taken against. */
 int oracle_rhs_magnitude_element(const oracle_ctx *c, const double *u, int jy, int ix, double *out)
 {
-    return rhs_element_impl(c, u, jy, ix, out, 1);
+    double gs[2];
+    if (c->alpha_global) {
+        int st = global_speeds(c, u, gs);
+        if (st) return st;
+    }
+    return rhs_element_impl(c, u, jy, ix, out, 1, c->alpha_global ? gs : NULL);
 }
 
-static int rhs_element_impl(const oracle_ctx *c, const double *u, int jy, int ix, double *out, int mag)
+static int rhs_element_impl(const oracle_ctx *c, const double *u, int jy, int ix, double *out, int mag,
+                            const double *gspeed)
 {
     int n = c->n, np = c->nphi, nf = c->nf;
     double r[3 * 81];
@@ -509,7 +564,7 @@ static int rhs_element_impl(const oracle_ctx *c, const double *u, int jy, int ix
             } else {
                 eval_point(c, mo, phio, qo);
                 eval_point(c, elem_modes(c, u, jnb, inb), phib, qb);
-                if (!numerical_flux(c, qo, qb, y, nxv, nyv, fn)) return ORACLE_ENONPHYSICAL;
+                if (!numerical_flux(c, qo, qb, y, nxv, nyv, gspeed, fn)) return ORACLE_ENONPHYSICAL;
             }
             double we = c->wg[k] * ejac;
             for (int m = 0; m < np; ++m) {
@@ -539,11 +594,18 @@ static int rhs_all(const oracle_ctx *c, const double *u, double *tend, int mag)
     int status = ORACLE_OK;
     int nel = c->nx * c->ny;
     size_t per = (size_t)c->nf * c->nphi;
+    double gs[2];
+    const double *gsp = NULL;
+    if (c->alpha_global) {
+        status = global_speeds(c, u, gs);
+        if (status) return status;
+        gsp = gs;
+    }
 #ifdef _OPENMP
 #pragma omp parallel for schedule(static) num_threads(c->nthreads) reduction(max : status)
 #endif
     for (int e = 0; e < nel; ++e) {
-        int st = rhs_element_impl(c, u, e / c->nx, e % c->nx, tend + (size_t)e * per, mag);
+        int st = rhs_element_impl(c, u, e / c->nx, e % c->nx, tend + (size_t)e * per, mag, gsp);
         if (st > status) status = st;
     }
     return status;

@@ -93,6 +93,7 @@ struct dg_ctx {
     double *d_result = nullptr;
     unsigned *d_status = nullptr;
     unsigned long long *d_maxbits = nullptr;
+    void *galpha = nullptr;   // global Rusanov mode: the stage's two speeds (2 values of T)
     double href = 0;      // reference depth of the resident state (FP32 path); 0 for FP64
     double t = 0;
     bool have_state = false;
@@ -208,6 +209,21 @@ int rk_plan(int order, StagePlan *pl)
     }
 }
 
+// Global Rusanov mode: the stage input's two speeds into h->galpha, then the
+// stage reads them (a.galpha).
+template <typename T>
+dg_status enqueue_global_speeds(dg_ctx *h, StageArgs<T> &a)
+{
+    if (!h->alpha_mode) return DG_OK;
+    if (cudaMemsetAsync(h->galpha, 0, 2 * sizeof(T), h->stream) != cudaSuccess ||
+        dg_launch_global_speeds<T>(h->n, a.base, a.inc, h->nlon, h->nlat, h->tc() ? 1 : 0, a.href, a.g,
+                                   static_cast<T *>(h->galpha), h->stream))
+        return fail(DG_ECUDA, "global speed kernel failed: %s", cudaGetErrorString(cudaGetLastError()));
+    a.galpha = static_cast<const T *>(h->galpha);
+    h->aux_launches += 1;
+    return DG_OK;
+}
+
 template <typename T>
 dg_status launch_step_t(dg_ctx *h, double dt, int cur, const RowTab<T> *rows)
 {
@@ -243,6 +259,7 @@ dg_status launch_step_t(dg_ctx *h, double dt, int cur, const RowTab<T> *rows)
                 h->aux_launches += 2;
             }
         }
+        if (dg_status gs = enqueue_global_speeds<T>(h, a)) return gs;
         int r;
         if constexpr (sizeof(T) == sizeof(float)) {
             r = h->tc() ? dg_launch_stage_tc(h->n, h->prec - DG_PREC_FP32_TC_BF16, a, h->stream)
@@ -467,7 +484,8 @@ dg_status dg_create(int nlon, int nlat, int degree, double radius, double g, dou
     if (cudaMalloc(&h->partials, 2 * sizeof(double) * h->nblocks) != cudaSuccess ||
         cudaMalloc(&h->d_result, sizeof(double)) != cudaSuccess ||
         cudaMalloc(&h->d_status, sizeof(unsigned)) != cudaSuccess ||
-        cudaMalloc(&h->d_maxbits, sizeof(unsigned long long)) != cudaSuccess) {
+        cudaMalloc(&h->d_maxbits, sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMalloc(&h->galpha, 2 * sizeof(double)) != cudaSuccess) {
         dg_destroy(h);
         return fail(DG_ENOMEM, "cudaMalloc failed");
     }
@@ -495,6 +513,7 @@ dg_status dg_destroy(dg_handle h)
     cudaFree(h->d_result);
     cudaFree(h->d_status);
     cudaFree(h->d_maxbits);
+    cudaFree(h->galpha);
     cudaFree(h->src);
     if (h->own_stream) cudaStreamDestroy(h->own_stream);
     dg_free_tables(h->tab);
@@ -556,12 +575,13 @@ dg_status dg_set_option(dg_handle h, int key, long long value)
         h->check = value ? 1 : 0;
         return DG_OK;
     case DG_OPT_ALPHA_MODE:
-        if (value == 0) {
-            h->alpha_mode = 0;
-            return DG_OK;
+        if (value != 0 && value != 1) return fail(DG_EINVAL, "unknown alpha mode %lld", value);
+        if (value != h->alpha_mode) {
+            CUDA_TRY(cudaStreamSynchronize(h->stream));
+            drop_graphs(h);
+            h->alpha_mode = (int)value;
         }
-        if (value == 1) return fail(DG_EUNSUPPORTED, "global Rusanov alpha is not built");
-        return fail(DG_EINVAL, "unknown alpha mode %lld", value);
+        return DG_OK;
     case DG_OPT_STREAM:
         CUDA_TRY(cudaStreamSynchronize(h->stream));
         h->stream = value ? reinterpret_cast<cudaStream_t>(value) : h->own_stream;
@@ -648,6 +668,7 @@ dg_status dg_rhs(dg_handle h, const double *modal_in, double *tend_out, size_t l
         StageArgs<double> a = base_args<double>(h, h->rows64, href);
         a.base = static_cast<double *>(in);
         a.out_rhs = static_cast<double *>(outb);
+        if (dg_status gs = enqueue_global_speeds<double>(h, a)) return gs;
         r = dg_launch_stage<double>(h->n, a, h->stream);
     } else if (h->tc()) {
         // stage in the lane-contiguous layout: input through SB[0], tendency in SB[1]
@@ -658,6 +679,7 @@ dg_status dg_rhs(dg_handle h, const double *modal_in, double *tend_out, size_t l
         StageArgs<float> a = base_args<float>(h, h->rows32, href);
         a.base = static_cast<float *>(h->SB[0]);
         a.out_rhs = static_cast<float *>(h->SB[1]);
+        if (dg_status gs = enqueue_global_speeds<float>(h, a)) return gs;
         r = dg_launch_stage_tc(h->n, h->prec - DG_PREC_FP32_TC_BF16, a, h->stream);
         if (!r) r = dg_launch_permute(static_cast<float *>(h->SB[1]), static_cast<float *>(outb), h->nlat, h->nlon,
                                       el, 0, h->stream);
@@ -671,6 +693,7 @@ dg_status dg_rhs(dg_handle h, const double *modal_in, double *tend_out, size_t l
                 return fail(DG_ECUDA, "learned source launch failed: %s", cudaGetErrorString(cudaGetLastError()));
             a.src = h->src;
         }
+        if (dg_status gs = enqueue_global_speeds<float>(h, a)) return gs;
         r = dg_launch_stage<float>(h->n, a, h->stream);
     }
     if (r) return fail(DG_ECUDA, "stage kernel launch failed: %s", cudaGetErrorString(cudaGetLastError()));

@@ -90,12 +90,13 @@ __device__ __forceinline__ void th_flux(const T *q, T href, T g, T *f, T &speed,
 // one-sided |u| + c; the cos(theta) of U = cos(theta) q cancels against the
 // 1/cos(theta) of the eigenvalue of dF/dU.  Scaled by cF = 2/(R dlambda).
 template <typename T>
-__device__ __forceinline__ void rusanov_lam(const T *L, const T *R, T href, T g, T cF, T *out, unsigned &st)
+__device__ __forceinline__ void rusanov_lam(const T *L, const T *R, T href, T g, T cF, T *out, unsigned &st,
+                                            T aglob = T(0))
 {
     T fl[3], fr[3], al, ar;
     lam_flux(L, href, g, fl, al, st);
     lam_flux(R, href, g, fr, ar, st);
-    const T a = fmax(al, ar);
+    const T a = aglob > T(0) ? aglob : fmax(al, ar);   // global mode: the stage's largest |u| + c
 #pragma unroll
     for (int f = 0; f < 3; ++f) out[f] = cF * (T(0.5) * (fl[f] + fr[f]) - T(0.5) * a * (R[f] - L[f]));
 }
@@ -103,12 +104,13 @@ __device__ __forceinline__ void rusanov_lam(const T *L, const T *R, T href, T g,
 // Rusanov flux through a theta-face, lower state S, upper state N, times the
 // edge cos(theta) ce (flux and jump of U both carry it); scaled by cG.
 template <typename T>
-__device__ __forceinline__ void rusanov_th(const T *S, const T *Nq, T href, T g, T cGce, T *out, unsigned &st)
+__device__ __forceinline__ void rusanov_th(const T *S, const T *Nq, T href, T g, T cGce, T *out, unsigned &st,
+                                           T aglob = T(0))
 {
     T fs[3], fn[3], as, an;
     th_flux(S, href, g, fs, as, st);
     th_flux(Nq, href, g, fn, an, st);
-    const T a = fmax(as, an);
+    const T a = aglob > T(0) ? aglob : fmax(as, an);   // global mode: the stage's largest |v| + c
 #pragma unroll
     for (int f = 0; f < 3; ++f) out[f] = cGce * (T(0.5) * (fs[f] + fn[f]) - T(0.5) * a * (Nq[f] - S[f]));
 }

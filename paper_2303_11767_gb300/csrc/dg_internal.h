@@ -83,6 +83,7 @@ struct StageArgs {
     T *out_base;
     T *out_lo;
     const T *src;    // optional modal source added to k (learned correction)
+    const T *galpha; // global Rusanov mode: [max |u| + c, max |v| + c] of the stage input; null = local
     const RowTab<T> *rows;
     unsigned int *status;
     int nlon, nlat;
@@ -162,6 +163,13 @@ template <typename T>
 int dg_launch_mass(const T *u, const T *lo, const double *c0, int nlon, int nlat, int n, double href,
                    double dlam, double dth, double scale, double *partials, int nblocks, double *result,
                    void *stream);
+// Global Rusanov speeds of the stage state base + inc (inc may be null): the
+// maxima of |u| + sqrt(g h) and |v| + sqrt(g h) over all Gauss points, as the
+// bits of T atomically maxed into out[0], out[1] (zero them first).  lanes:
+// the state is [lat][field][mode][lon] instead of [lat][lon][field][mode].
+template <typename T>
+int dg_launch_global_speeds(int n, const T *base, const T *inc, int nlon, int nlat, int lanes, T href, T g, T *out,
+                            void *stream);
 template <typename T>
 int dg_launch_max_speed(const T *u, int nlon, int nlat, int n, double href, double g,
                         unsigned long long *maxbits, unsigned int *status, void *stream);

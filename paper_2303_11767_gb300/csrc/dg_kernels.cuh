@@ -189,6 +189,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &A, int bx, int by
     T *wb = wbuf + (warp * G + (lane_ok ? g : 0)) * WB;
 
     const RowTab<T> *RT = A.rows + (valid ? j : 0);
+    const T ga_l = A.galpha ? A.galpha[0] : T(0), ga_t = A.galpha ? A.galpha[1] : T(0);
 
     // ---- S0: own modal row b = k of the stage state
     T uh[3][N];
@@ -347,14 +348,14 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &A, int bx, int by
             const T *tW = trc + (own - 1) * TRC;
 #pragma unroll
             for (int f = 0; f < 3; ++f) nb[f] = tW[(1 * 3 + f) * N + k];       // W neighbour's E trace
-            rusanov_lam(nb, tr[0], href, gg, A.cF, fx, st);
+            rusanov_lam(nb, tr[0], href, gg, A.cF, fx, st, ga_l);
 #pragma unroll
             for (int f = 0; f < 3; ++f) ef[(own * 2 + 0) * 3 * N + f * N + k] = fx[f];
             if (j > 0) {
                 const T *tS = trc + (own - TW) * TRC;
 #pragma unroll
                 for (int f = 0; f < 3; ++f) nb[f] = tS[(3 * 3 + f) * N + k];   // S neighbour's N trace
-                rusanov_th(nb, tr[2], href, gg, A.cG * __ldg(&RT->ce_s), fx, st);
+                rusanov_th(nb, tr[2], href, gg, A.cG * __ldg(&RT->ce_s), fx, st, ga_t);
             } else {
 #pragma unroll
                 for (int f = 0; f < 3; ++f) fx[f] = T(0);                       // pole edge: zero flux
@@ -374,7 +375,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &A, int bx, int by
                     L[f] = trc[sl * TRC + (1 * 3 + f) * N + kk];
                     R[f] = trc[sr * TRC + (0 * 3 + f) * N + kk];
                 }
-                rusanov_lam(L, R, href, gg, A.cF, fx, st);
+                rusanov_lam(L, R, href, gg, A.cF, fx, st, ga_l);
 #pragma unroll
                 for (int f = 0; f < 3; ++f) ef[(sr * 2 + 0) * 3 * N + f * N + kk] = fx[f];
             } else {                            // N edge of the top valid row
@@ -385,7 +386,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &A, int bx, int by
                     L[f] = trc[sl * TRC + (3 * 3 + f) * N + kk];
                     R[f] = trc[su * TRC + (2 * 3 + f) * N + kk];
                 }
-                rusanov_th(L, R, href, gg, A.cG * __ldg(&A.rows[j0 + Wv - 1].ce_n), fx, st);
+                rusanov_th(L, R, href, gg, A.cG * __ldg(&A.rows[j0 + Wv - 1].ce_n), fx, st, ga_t);
 #pragma unroll
                 for (int f = 0; f < 3; ++f) ef[(su * 2 + 1) * 3 * N + f * N + kk] = fx[f];
             }
@@ -612,6 +613,8 @@ __global__ void __launch_bounds__(32 * W, 24 / W) ensemble_kernel(const EnsArgs<
         A.out_base = E.out_base ? E.out_base + m.off : nullptr;
         A.out_lo = E.out_lo ? E.out_lo + m.off : nullptr;
         A.rows = E.rows + m.rows;
+        A.src = nullptr;
+        A.galpha = nullptr;
         A.status = E.status;
         A.nlon = m.nlon;
         A.nlat = m.nlat;
@@ -810,9 +813,96 @@ __global__ void max_speed_kernel(const T *__restrict__ u, int nel, double href, 
     if (st) atomicOr(status, st);
 }
 
+__device__ __forceinline__ void atomic_max_pos(float *a, float v)
+{
+    atomicMax(reinterpret_cast<unsigned *>(a), __float_as_uint(v));
+}
+__device__ __forceinline__ void atomic_max_pos(double *a, double v)
+{
+    atomicMax(reinterpret_cast<unsigned long long *>(a), (unsigned long long)__double_as_longlong(v));
+}
+
+// Global Rusanov speeds of the stage state base + inc: the maxima of
+// |u| + sqrt(g h) and |v| + sqrt(g h) over every Gauss point (one thread per
+// element; non-physical points are left to the stage kernel to report).
+// Positive floating-point values order like their bit patterns, so the
+// atomic maxima on the bits are exact and order independent.
+template <typename T, int N>
+__global__ void global_speeds_kernel(const T *__restrict__ base, const T *__restrict__ inc, int nlon, int nel,
+                                     int lanes, T href, T g, T *out)
+{
+    constexpr int NP = N * N, EL = 3 * NP;
+    const BasisTab<T> &B = c_basis[N - 1];
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    T su = T(0), sv = T(0);
+    if (e < nel) {
+        const int j = e / nlon, i = e - j * nlon;
+        const size_t o0 = lanes ? (size_t)j * EL * nlon + i : (size_t)e * EL;
+        const size_t ms = lanes ? (size_t)nlon : 1;
+        T u[EL];
+#pragma unroll
+        for (int c = 0; c < EL; ++c) {
+            u[c] = __ldg(base + o0 + c * ms);
+            if (inc) u[c] += __ldg(inc + o0 + c * ms);
+        }
+#pragma unroll
+        for (int be = 0; be < N; ++be)
+#pragma unroll
+            for (int al = 0; al < N; ++al) {
+                T qv[3];
+#pragma unroll
+                for (int f = 0; f < 3; ++f) {
+                    T s = T(0);
+#pragma unroll
+                    for (int b = 0; b < N; ++b) {
+                        T t = T(0);
+#pragma unroll
+                        for (int a = 0; a < N; ++a) t = fma(B.LV[a][al], u[f * NP + b * N + a], t);
+                        s = fma(B.LV[b][be], t, s);
+                    }
+                    qv[f] = s;
+                }
+                const T h = href + qv[0];
+                if (!(h > T(0))) continue;
+                const T c = sqrt(g * h);
+                su = fmax(su, fabs(qv[1] / h) + c);
+                sv = fmax(sv, fabs(qv[2] / h) + c);
+            }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        su = fmax(su, __shfl_xor_sync(0xffffffffu, su, o));
+        sv = fmax(sv, __shfl_xor_sync(0xffffffffu, sv, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (su > T(0)) atomic_max_pos(out, su);
+        if (sv > T(0)) atomic_max_pos(out + 1, sv);
+    }
+}
+
 }  // namespace dgk
 
 // ------------------------------------------------------ host-side launchers --
+
+template <>
+int dg_launch_global_speeds<DG_REAL>(int n, const DG_REAL *base, const DG_REAL *inc, int nlon, int nlat, int lanes,
+                                     DG_REAL href, DG_REAL g, DG_REAL *out, void *stream)
+{
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int nel = nlon * nlat;
+    const int threads = 128;
+    const int blocks = (nel + threads - 1) / threads;
+#define DG_GS(NN) dgk::global_speeds_kernel<DG_REAL, NN><<<blocks, threads, 0, s>>>(base, inc, nlon, nel, lanes, href, g, out)
+    switch (n) {
+    case 1: DG_GS(1); break;
+    case 2: DG_GS(2); break;
+    case 3: DG_GS(3); break;
+    case 4: DG_GS(4); break;
+    case 5: DG_GS(5); break;
+    default: return 1;
+    }
+#undef DG_GS
+    return cudaPeekAtLastError() == cudaSuccess ? 0 : 1;
+}
 
 template <>
 int dg_upload_basis<DG_REAL>(const BasisTab<double> *all)

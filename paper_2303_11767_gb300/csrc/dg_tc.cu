@@ -282,6 +282,7 @@ __global__ void __launch_bounds__(128 * TC_TPE, 2) tc_stage_kernel(const StageAr
     const uint32_t rowoff = (uint32_t)(32 * q4 + l) * 16;
     unsigned char *const opA = sm + SM::A;
     const RowTab<float> *const RT = A.rows + j;
+    float ga_l = 0.0f, ga_t = 0.0f;   // global Rusanov speeds (0 = local mode), read after the dependency wait
 
     // prologue (independent of the previous kernel's results): tensor
     // memory, the completion barrier, the two basis operands
@@ -290,6 +291,10 @@ __global__ void __launch_bounds__(128 * TC_TPE, 2) tc_stage_kernel(const StageAr
     for (int c = tid; c < (int)(SM::SZ_B1 / 16); c += NT) reinterpret_cast<uint4 *>(sm + SM::B1)[c] = __ldg(gB1 + c);
     for (int c = tid; c < (int)(SM::SZ_B2 / 16); c += NT) reinterpret_cast<uint4 *>(sm + SM::B2)[c] = __ldg(gB2 + c);
     dgk::pdl_wait();
+    if (A.galpha) {
+        ga_l = __ldg(A.galpha);
+        ga_t = __ldg(A.galpha + 1);
+    }
 
     // ---- S0: 8 modes (chunk c) of one field of the stage state u = base + inc
     //      of one element -> its row of a GEMM1 operand (zeros where missing)
@@ -414,7 +419,7 @@ __global__ void __launch_bounds__(128 * TC_TPE, 2) tc_stage_kernel(const StageAr
                 L[f] = __shfl_up_sync(0xffffffffu, twe[f][N + k], 1);
                 R[f] = twe[f][k];
             }
-            dgk::rusanov_lam(L, R, href, gg, A.cF, o, sw);
+            dgk::rusanov_lam(L, R, href, gg, A.cF, o, sw, ga_l);
 #pragma unroll
             for (int f = 0; f < 3; ++f) efW[f][k] = o[f];
         }
@@ -487,7 +492,7 @@ __global__ void __launch_bounds__(128 * TC_TPE, 2) tc_stage_kernel(const StageAr
                 Sq[f] = q4 > 0 ? XN[(((q4 - 1) * 3 + f) * N + k) * 32 + l] : halo[f][k];
                 Nq[f] = tsn[f][k];
             }
-            dgk::rusanov_th(Sq, Nq, href, gg, cgs, o, ss);
+            dgk::rusanov_th(Sq, Nq, href, gg, cgs, o, ss, ga_t);
 #pragma unroll
             for (int f = 0; f < 3; ++f) efS[f][k] = j0 + q4 > 0 ? o[f] : 0.0f;   // pole edge: zero flux
         }
@@ -521,7 +526,7 @@ __global__ void __launch_bounds__(128 * TC_TPE, 2) tc_stage_kernel(const StageAr
                     Sq[f] = tsn[f][N + k];
                     Nq[f] = halo[f][k];
                 }
-                dgk::rusanov_th(Sq, Nq, href, gg, cgn, o, sn);
+                dgk::rusanov_th(Sq, Nq, href, gg, cgn, o, sn, ga_t);
 #pragma unroll
                 for (int f = 0; f < 3; ++f) efN[f][k] = o[f];
             }

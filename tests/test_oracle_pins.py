@@ -156,11 +156,12 @@ def test_rk_step_is_taylor_polynomial_on_linear_ode(order):
 
 # ------------------------------------------- p = 0: finite volume brute force --
 
-def _fv_rhs(q, nlon, nlat):
+def _fv_rhs(q, nlon, nlat, global_alpha=False):
     """Brute-force first-order finite volume update that DG with p = 0 must
     reproduce: cell value q, cos(theta)-weighted exact cell area, Rusanov flux
     at edge midpoints with the q-jump coefficients (|u|+c)/R and
-    cos(theta_e)(|v|+c)/R, zero flux at the poles, midpoint-rule sources."""
+    cos(theta_e)(|v|+c)/R, zero flux at the poles, midpoint-rule sources.
+    global_alpha: the two speeds are the maxima over all cells instead."""
     dl, dth = 2 * math.pi / nlon, math.pi / nlat
     out = np.zeros_like(q)
 
@@ -172,8 +173,13 @@ def _fv_rhs(q, nlon, nlat):
         h, hu, hv = s
         return math.cos(th) * np.array([hv, hu * hv / h, hv * hv / h + 0.5 * G * h * h]) / R
 
-    def spd(s, k):
+    def spd_local(s, k):
         return abs(s[k] / s[0]) + math.sqrt(G * s[0])
+
+    gmax = {k: max(spd_local(q[j, i], k) for j in range(nlat) for i in range(nlon)) for k in (1, 2)}
+
+    def spd(s, k):
+        return gmax[k] if global_alpha else spd_local(s, k)
 
     for j in range(nlat):
         tb = -math.pi / 2 + j * dth
@@ -212,6 +218,41 @@ def test_p0_reduces_to_finite_volume_rusanov():
     k = o.rhs((2.0 * q)[..., None])[..., 0] / 2.0
     want = _fv_rhs(q, nlon, nlat)
     np.testing.assert_allclose(k, want, rtol=1e-12, atol=1e-14 * np.abs(want).max(axis=(0, 1)).max())
+
+
+def test_p0_global_alpha_reduces_to_finite_volume_rusanov():
+    """The global Rusanov mode at p = 0: one Gauss point per cell, so the
+    global speeds are the maxima over the cell values."""
+    nlon, nlat = 6, 3
+    rng = np.random.default_rng(12)
+    q = np.zeros((nlat, nlon, 3))
+    q[..., 0] = 5000 + 500 * rng.random((nlat, nlon))
+    q[..., 1] = q[..., 0] * rng.normal(0, 15, (nlat, nlon))
+    q[..., 2] = q[..., 0] * rng.normal(0, 15, (nlat, nlon))
+    o = sphere(nlon, nlat, 0)
+    o.set_alpha_mode(1)
+    k = o.rhs((2.0 * q)[..., None])[..., 0] / 2.0
+    want = _fv_rhs(q, nlon, nlat, global_alpha=True)
+    np.testing.assert_allclose(k, want, rtol=1e-12, atol=1e-14 * np.abs(want).max(axis=(0, 1)).max())
+    # and it differs from the local mode (the speeds are not all equal)
+    assert np.abs(want - _fv_rhs(q, nlon, nlat)).max() > 1e-6 * np.abs(want).max()
+
+
+def test_global_alpha_mode_keeps_mass_and_matches_local_for_uniform_speeds():
+    nlon, nlat, p = 12, 6, 2
+    o = sphere(nlon, nlat, p)
+    o.set_alpha_mode(1)
+    u = o.project_tensor(synth.SmoothField(3).fields_grid)
+    m0 = o.total_mass(u)
+    m1 = o.total_mass(o.step(u, 20, o.max_dt(u, 0.1), 3))
+    assert abs(m1 / m0 - 1) < 1e-13
+    # rest state: every speed is sqrt(g h0), global = local
+    rest = np.zeros_like(u)
+    rest[..., 0, 0] = 2 * 5000.0
+    o_loc = sphere(nlon, nlat, p)
+    np.testing.assert_allclose(o.rhs(rest), o_loc.rhs(rest), rtol=0, atol=1e-12 * np.abs(o_loc.rhs(rest)).max())
+    with pytest.raises(ValueError):
+        O.Oracle.plane_advection(4, 4, 1).set_alpha_mode(1)
 
 
 # ----------------------------------------------------- conservation and rest --

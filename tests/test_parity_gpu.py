@@ -138,6 +138,40 @@ def test_rk_orders(order):
         assert_within(state_err(s.get_state(), want), 1e-12, f"RK{order}")
 
 
+# ---------------------------------------------------- global Rusanov alpha --
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32", 1e-5), ("fp32_tc_fp16", 8 * 2.0 ** -12)])
+def test_global_alpha_mode_matches_oracle(prec, tol):
+    nlon, nlat, p = 44, 14, 3
+    o = oracle_sphere(nlon, nlat, p)
+    o.set_alpha_mode(1)
+    u = o.project_tensor(synth.SmoothField(13).fields_grid)
+    dt = o.max_dt(u, 0.1)
+    want = o.step(u, 12, dt, 3)
+    with solver(nlon, nlat, p, prec) as s:
+        k_local = s.rhs(u)
+        s.set_option(dgswe.OPT_ALPHA_MODE, 1)
+        k = s.rhs(u)
+        S = o.rhs_magnitude(u)
+        assert_within(tend_err(k, o.rhs(u), S), tol, f"global-alpha rhs {prec}")
+        if prec == "fp64":   # the switch changes the tendency as it does in the oracle
+            o_loc = oracle_sphere(nlon, nlat, p)
+            d_or = o.rhs(u) - o_loc.rhs(u)
+            assert np.abs((k - k_local) - d_or).max() <= 0.05 * np.abs(d_or).max()
+        s.set_option(dgswe.OPT_STEPS_PER_GRAPH, 4)
+        s.set_state(u)
+        m0 = s.total_mass()
+        s.step(12, dt)
+        got = s.get_state()
+        assert abs(s.total_mass() / m0 - 1) < (1e-13 if prec == "fp64" else 1e-9)
+    if prec == "fp32_tc_fp16":
+        for f in range(3):
+            d = np.abs(got[..., f, :] - want[..., f, :]).max()
+            assert d <= 12 * dt * tol * S[..., f, :].max() + 1e-5 * np.abs(want[..., f, :]).max()
+    else:
+        assert_within(state_err(got, want), tol, f"global-alpha 12 steps {prec}")
+
+
 # ------------------------------------------------------------- diagnostics --
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
@@ -222,7 +256,7 @@ def test_nonphysical_and_nonfinite_are_reported(prec):
 def test_option_errors():
     with solver(8, 4, 1, "fp64") as s:
         for key, val, status in [(dgswe.OPT_PRECISION, 7, dgswe.DG_EINVAL),
-                                 (dgswe.OPT_ALPHA_MODE, 1, dgswe.DG_EUNSUPPORTED),
+                                 (dgswe.OPT_ALPHA_MODE, 2, dgswe.DG_EINVAL),
                                  (dgswe.OPT_RK_ORDER, 5, dgswe.DG_EINVAL),
                                  (99, 0, dgswe.DG_EINVAL)]:
             with pytest.raises(dgswe.DGError) as e:
