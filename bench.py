@@ -219,6 +219,26 @@ def cpu_leg(nlon, nlat, p, seed, budget_s, max_steps):
     return dict(o=o, u0=u0, u1=u1, dt=dt, nsteps=nsteps, wall=wall, cores=cores)
 
 
+def stage_flops_per_dof(n):
+    """Algorithmic flops of one sum-factorised stage per DOF-update (MAC = 2):
+    eval 6n^3 + volume 14n^3 MACs, traces and lifts 36n^2 MACs, ~30 flops of
+    fluxes and sources per Gauss point, ~50 per Rusanov point (2n per
+    element), 5 per DOF for the RK update: (40n^3 + 117n^2 + 100n) / (3n^2)."""
+    return (40.0 * n ** 3 + 117.0 * n ** 2 + 100.0 * n) / (3.0 * n ** 2)
+
+
+def cpu_model():
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
 def field_errors(x, y):
     return [float(np.linalg.norm(x[..., f, :] - y[..., f, :]) / np.linalg.norm(y[..., f, :])) for f in range(3)]
 
@@ -419,8 +439,14 @@ def main():
         k64 = max(2, args.steps // 5)
         t64 = time_device(s64, torch, stream, nsteps, dt, k64, 1, mass_t, flush)
         v64 = dof * 3 * nsteps * k64 / (sum(t64) * 1e-3)
+        fp64_peak = dgswe.measure_fp64_peak(5)
+        fpd = stage_flops_per_dof(p + 1)
         out["fp64_plain"] = {"value": v64, "ms_per_step": sum(t64) / k64, "dtype": "f64", "steps": k64,
-                             "speedup_of_value": value / v64}
+                             "speedup_of_value": value / v64,
+                             "roofline": {"bound": "alu", "achieved": v64 * fpd / 1e9, "peak": fp64_peak,
+                                          "unit": "GFLOP/s", "frac": v64 * fpd / 1e9 / fp64_peak,
+                                          "peak_kind": "measured FP64 FMA probe (dg_measure_fp64_peak)",
+                                          "flops_per_dof": fpd}}
 
         # ---- the tensor-core precisions on the same workload (device-timed)
         for tcp in ("fp32_tc_bf16", "fp32_tc_fp16"):
@@ -457,10 +483,17 @@ def main():
         # ---- the oracle on the host cores (bounded sample) and the L2 error
         leg = cpu_leg(nlon, nlat, p, seed, budget_s=15.0, max_steps=nsteps)
         cpu_value = dof * 3 * leg["nsteps"] / leg["wall"]
+        o1 = leg["o"]
+        o1.set_threads(1)
+        t0 = time.perf_counter()
+        for _ in range(3):
+            o1.rhs(leg["u0"])
+        single = 3 * dof / (time.perf_counter() - t0)
         out["cpu_baseline"] = {"value": cpu_value, "unit": "DOF-updates/s", "cores": leg["cores"], "kind": "oracle",
                                "sample": f"{leg['nsteps']} SSP-RK3 steps of the same workload "
                                          f"({3 * leg['nsteps']} stages), FP64, {leg['cores']} threads",
-                               "seconds": leg["wall"]}
+                               "seconds": leg["wall"], "cpu": cpu_model(),
+                               "single_thread": {"value": single, "sample": "3 right-hand sides, 1 thread"}}
         errs = {}
         for prec in sorted({"fp32", "fp64", "fp32_tc_bf16", "fp32_tc_fp16", args.precision}):
             sv = make(prec)

@@ -287,6 +287,12 @@ dg_status dg_max_dt_noalloc(const double *d_modal, int nlon, int nlat, int degre
  * returned.  Synchronous.  DG_ETIMEOUT if the tensor cores did not answer. */
 dg_status dg_tc_check_contraction(int degree, int op, const float *d_a, float *d_out, int *n1, int *k1);
 
+/* Measured FP64 arithmetic peak of the current device in GFLOP/s: the best of
+ * `reps` timed launches of a kernel of independent double-precision FMA chains
+ * over every SM (2 flops per FMA).  The roof of the FP64 stage, which on GB300
+ * is bound by FP64 arithmetic rather than by HBM.  Synchronous. */
+dg_status dg_measure_fp64_peak(int reps, double *gflops);
+
 /* Number of fused stage-kernel launches issued by this handle so far. */
 long long dg_stage_launches(dg_handle h);
 

@@ -983,6 +983,14 @@ dg_status dg_tc_check_contraction(int degree, int op, const float *d_a, float *d
     return DG_OK;
 }
 
+dg_status dg_measure_fp64_peak(int reps, double *gflops)
+{
+    if (!gflops || reps < 1) return fail(DG_EINVAL, "need reps >= 1 and gflops");
+    if (dg_probe_fp64_gflops(reps, gflops))
+        return fail(DG_ECUDA, "FP64 probe failed: %s", cudaGetErrorString(cudaGetLastError()));
+    return DG_OK;
+}
+
 dg_status dg_get_time(dg_handle h, double *t)
 {
     if (dg_status s = check(h)) return s;

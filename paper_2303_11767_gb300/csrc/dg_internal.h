@@ -192,6 +192,9 @@ int dg_mlp_launch_source(const dg_mlp_ctx *m, const float *base, const float *in
                          const double *c0, float *src, void *stream);
 bool dg_mlp_shape_is(const dg_mlp_ctx *m, int nin, int h, int nout);
 
+// dg_probe.cu: measured FP64 FMA rate of the current device (GFLOP/s).
+int dg_probe_fp64_gflops(int reps, double *gflops);
+
 // dg_api.cpp: set the calling thread's message returned by dg_last_error().
 void dg_set_last_error(const char *msg);
 // dg_api.cpp: make sure the constant basis tables are on device `device`

@@ -53,6 +53,7 @@ SIGNATURES = {
     "dg_max_dt_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                          ctypes.c_double, ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p]),
     "dg_last_error": (ctypes.c_char_p, [_H]),
+    "dg_measure_fp64_peak": (ctypes.c_int, [ctypes.c_int, _dp]),
     "dg_tc_check_contraction": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
                                                ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
     "dg_mlp_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_ulonglong,
@@ -122,6 +123,13 @@ def _check(status, h=None):
 
 def set_device(device: int):
     _check(lib().dg_set_device(int(device)))
+
+
+def measure_fp64_peak(reps: int = 5) -> float:
+    """Measured FP64 FMA rate of the current device, GFLOP/s."""
+    v = ctypes.c_double(0.0)
+    _check(lib().dg_measure_fp64_peak(int(reps), ctypes.byref(v)))
+    return v.value
 
 
 def tc_contraction_shape(degree: int, op: int):
