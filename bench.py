@@ -37,6 +37,13 @@ WORKLOADS = {
 ENSEMBLE_DESC = ("256 members, nlat uniform on 20..180, nlon = 2 nlat, degree uniform on 1..4, "
                  "member k seed 1000+k, FP32 SSP-RK3, 10 steps per bench step, one persistent launch per stage")
 METRIC = "DOF-updates/s per RK stage (FP32/TC/learned vs FP64 plain) at stated L2 error"
+# DRAM bytes per stage launch of the timed kernel, from one ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum, mean over the three SSP-RK3
+# stages, cold cache); only for kernels unchanged since that capture.
+TRAFFIC = {
+    ("fp32", "c2"): (6306624.0, "3.20 / 6.31 / 9.42 MB read, 0 written (the 3.1 MB state arrays stay in L2)"),
+    ("fp32_tc_bf16", "c3"): (40443000.0, "19.6 / 39.0 / 58.5 MB read, 0 / 0.2 / 4.0 MB written"),
+}
 CFL = 0.1
 FLUSH_BYTES = 256 << 20
 # precision -> arithmetic of the path ("+bf16tc": FP32 stage arithmetic with the
@@ -413,8 +420,11 @@ def main():
     launch_s = (sum(times) * 1e-3) / max(1, stage_launches_timed)
     peak, peak_kind = peaks()
     achieved = bytes_per_launch / launch_s / 1e9
+    traffic = TRAFFIC.get((args.precision, args.workload))
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": None, "peak_kind": peak_kind, "kernel": KERNELS[args.precision].format(n=p + 1),
+                "traffic": traffic[0] if traffic else None,
+                "traffic_note": traffic[1] if traffic else "no capture of this kernel and workload",
+                "peak_kind": peak_kind, "kernel": KERNELS[args.precision].format(n=p + 1),
                 "bytes_per_launch": bytes_per_launch, "launch_us": launch_s * 1e6}
 
     out = {

@@ -100,6 +100,18 @@ dg_status dg_set_device(int device);
 dg_status dg_create(int nlon, int nlat, int degree, double radius, double g, double omega,
                     dg_handle *out);
 
+/* The paper's planar validation problem (Sec. 4.1, Eq. lin_adv): linear
+ * advection du/dt + div(beta u) = 0 of one scalar on the unit square,
+ * periodic in both directions, nx x ny elements of degree 0..4, FP64, beta =
+ * (bx, by); alpha_speed 1: Rusanov alpha = |beta|, 0: |beta . n| (upwind).
+ * State layout [y j][x i][mode m = b*n + a], dg_state_len = nx ny (p+1)^2.
+ * The handle supports dg_set_state(_device), dg_get_state(_device), dg_rhs,
+ * dg_step (DG_OPT_RK_ORDER 1..4, graphs), DG_OPT_RK_ORDER / STEPS_PER_GRAPH /
+ * STREAM / CHECK_FINITE, dg_get_time / dg_set_time and dg_destroy; the
+ * sphere-only calls return DG_EUNSUPPORTED. */
+dg_status dg_create_plane_advection(int nx, int ny, int degree, double bx, double by, int alpha_speed,
+                                    dg_handle *out);
+
 /* Free the handle and its device buffers.  NULL is accepted. */
 dg_status dg_destroy(dg_handle h);
 

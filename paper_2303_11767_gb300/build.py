@@ -17,7 +17,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I" + os.path.join(HERE, "..", "include")]
 SOURCES = ["dg_kernels_f32.cu", "dg_kernels_f64.cu", "dg_api.cpp", "dg_tables.cpp", "dg_noalloc.cu",
-           "dg_ensemble.cpp", "dg_mlp.cu", "dg_restrict.cu", "dg_tc.cu", "dg_probe.cu"]
+           "dg_ensemble.cpp", "dg_mlp.cu", "dg_restrict.cu", "dg_tc.cu", "dg_probe.cu", "dg_plane.cu"]
 
 
 def _deps():

@@ -67,6 +67,7 @@ unsigned long long g_basis_uploaded = 0;   // per-device bit: constant tables pr
 }  // namespace
 
 struct dg_ctx {
+    int physics = 0;   // 0: shallow water on the sphere; 1: planar linear advection (one scalar)
     int nlon = 0, nlat = 0, p = 0, n = 0, nphi = 0;
     size_t nel = 0, len = 0;
     double R = 0, g = 0, omega = 0;
@@ -102,6 +103,9 @@ struct dg_ctx {
     dg_mlp_ctx *mlp = nullptr;    // learned source term (degree 1, FP32)
     float *src = nullptr;         // its per-stage modal output
     std::vector<GraphEntry> graphs;
+    double bx = 0, by = 0;       // planar advection velocity
+    int alpha_speed = 0;         // planar: Rusanov alpha = |beta| (1) or |beta . n| (0)
+    BasisTab<double> pbasis{};   // planar: basis tables of degree p
     bool f32() const { return prec != DG_PREC_FP64; }                 // FP32 storage
     bool tc() const { return prec == DG_PREC_FP32_TC_BF16 || prec == DG_PREC_FP32_TC_FP16; }
 };
@@ -209,6 +213,28 @@ int rk_plan(int order, StagePlan *pl)
     }
 }
 
+// Planar advection stage with the FP64 stage semantics of `a`.
+int launch_plane(dg_ctx *h, const StageArgs<double> &a)
+{
+    PlaneArgs pa;
+    pa.s = a;
+    pa.basis = h->pbasis;
+    pa.bx = h->bx;
+    pa.by = h->by;
+    pa.cx = 2.0 * h->nlon;   // 2 / dx on the unit square
+    pa.cy = 2.0 * h->nlat;
+    pa.nx = h->nlon;
+    pa.ny = h->nlat;
+    pa.alpha_speed = h->alpha_speed;
+    return dg_launch_stage_plane(h->n, pa, h->stream);
+}
+
+dg_status planar_unsupported(dg_ctx *h, const char *what)
+{
+    (void)h;
+    return fail(DG_EUNSUPPORTED, "%s is not available for planar advection", what);
+}
+
 // Global Rusanov mode: the stage input's two speeds into h->galpha, then the
 // stage reads them (a.galpha).
 template <typename T>
@@ -265,7 +291,7 @@ dg_status launch_step_t(dg_ctx *h, double dt, int cur, const RowTab<T> *rows)
             r = h->tc() ? dg_launch_stage_tc(h->n, h->prec - DG_PREC_FP32_TC_BF16, a, h->stream)
                         : dg_launch_stage<T>(h->n, a, h->stream);
         } else {
-            r = dg_launch_stage<T>(h->n, a, h->stream);
+            r = h->physics == 1 ? launch_plane(h, a) : dg_launch_stage<T>(h->n, a, h->stream);
         }
         if (r) return fail(DG_ECUDA, "stage kernel launch failed: %s", cudaGetErrorString(cudaGetLastError()));
         h->launches++;
@@ -498,6 +524,63 @@ dg_status dg_create(int nlon, int nlat, int degree, double radius, double g, dou
     return DG_OK;
 }
 
+dg_status dg_create_plane_advection(int nx, int ny, int degree, double bx, double by, int alpha_speed,
+                                    dg_handle *out)
+{
+    if (!out) return fail(DG_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (nx < 1 || ny < 1) return fail(DG_EINVAL, "need nx, ny >= 1 (got %d, %d)", nx, ny);
+    if (degree < 0 || degree > DG_MAXN - 1) return fail(DG_EINVAL, "degree must be in [0, %d]", DG_MAXN - 1);
+    if (!std::isfinite(bx) || !std::isfinite(by)) return fail(DG_EINVAL, "beta must be finite");
+    if (alpha_speed != 0 && alpha_speed != 1) return fail(DG_EINVAL, "alpha_speed must be 0 or 1");
+    if ((double)nx * ny > 2.0e9) return fail(DG_EINVAL, "mesh too large");
+    dg_ctx *h = new (std::nothrow) dg_ctx;
+    if (!h) return fail(DG_ENOMEM, "host allocation failed");
+    h->physics = 1;
+    h->nlon = nx;
+    h->nlat = ny;
+    h->p = degree;
+    h->n = degree + 1;
+    h->nphi = h->n * h->n;
+    h->nel = (size_t)nx * ny;
+    h->len = h->nel * h->nphi;
+    h->R = 1.0;
+    h->bx = bx;
+    h->by = by;
+    h->alpha_speed = alpha_speed;
+    if (cudaGetDevice(&h->device) != cudaSuccess) {
+        delete h;
+        return fail(DG_ECUDA, "no CUDA device: %s", cudaGetErrorString(cudaGetLastError()));
+    }
+    {
+        HostTables t;
+        if (dg_build_tables(t, 1, 2, degree, 1.0, 1.0)) {
+            dg_free_tables(t);
+            delete h;
+            return fail(DG_EINVAL, "basis table construction failed");
+        }
+        h->pbasis = t.basis;
+        dg_free_tables(t);
+    }
+    dg_status st = DG_OK;
+    if (cudaStreamCreateWithFlags(&h->own_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        dg_destroy(h);
+        return fail(DG_ECUDA, "stream creation failed");
+    }
+    h->stream = h->own_stream;
+    if ((st = alloc_state_buffers(h)) != DG_OK) {
+        dg_destroy(h);
+        return st;
+    }
+    if (cudaMalloc(&h->d_status, sizeof(unsigned)) != cudaSuccess ||
+        cudaMemset(h->d_status, 0, sizeof(unsigned)) != cudaSuccess) {
+        dg_destroy(h);
+        return fail(DG_ENOMEM, "cudaMalloc failed");
+    }
+    *out = h;
+    return DG_OK;
+}
+
 dg_status dg_destroy(dg_handle h)
 {
     if (!h) return DG_OK;
@@ -531,6 +614,8 @@ dg_status dg_set_option(dg_handle h, int key, long long value)
 {
     if (dg_status s = check(h)) return s;
     DeviceGuard dg(h->device);
+    if (h->physics == 1 && ((key == DG_OPT_PRECISION && value != DG_PREC_FP64) || (key == DG_OPT_ALPHA_MODE && value)))
+        return planar_unsupported(h, key == DG_OPT_PRECISION ? "a precision other than FP64" : "the global alpha mode");
     switch (key) {
     case DG_OPT_PRECISION: {
         if (value < DG_PREC_FP64 || value > DG_PREC_FP32_TC_FP16) return fail(DG_EINVAL, "unknown precision %lld", value);
@@ -601,6 +686,13 @@ dg_status dg_set_state_device(dg_handle h, const double *d_modal, size_t len)
     if (dg_status s = check(h)) return s;
     if (!d_modal || len != h->len) return fail(DG_EINVAL, "state length %zu, expected %zu", len, h->len);
     DeviceGuard dg(h->device);
+    if (h->physics == 1) {
+        CUDA_TRY(cudaMemcpyAsync(h->B[0], d_modal, len * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+        h->cur = 0;
+        h->href = 0.0;
+        h->have_state = true;
+        return DG_OK;
+    }
     CUDA_TRY(cudaMemcpyAsync(h->stage64, d_modal, len * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
     h->href = 0.0;
     if (h->f32()) {
@@ -623,6 +715,14 @@ dg_status dg_set_state(dg_handle h, const double *modal, size_t len)
     if (dg_status s = check(h)) return s;
     if (!modal || len != h->len) return fail(DG_EINVAL, "state length %zu, expected %zu", len, h->len);
     DeviceGuard dg(h->device);
+    if (h->physics == 1) {
+        CUDA_TRY(cudaMemcpyAsync(h->B[0], modal, len * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+        CUDA_TRY(cudaStreamSynchronize(h->stream));
+        h->cur = 0;
+        h->href = 0.0;
+        h->have_state = true;
+        return DG_OK;
+    }
     CUDA_TRY(cudaMemcpyAsync(h->stage64, modal, len * sizeof(double), cudaMemcpyHostToDevice, h->stream));
     h->href = h->f32() ? mean_depth(modal, h->nel, h->nphi) : 0.0;
     h->cur = 0;
@@ -638,6 +738,10 @@ dg_status dg_get_state_device(dg_handle h, double *d_modal, size_t len)
     if (!d_modal || len != h->len) return fail(DG_EINVAL, "state length %zu, expected %zu", len, h->len);
     if (!h->have_state) return fail(DG_EINVAL, "no state set");
     DeviceGuard dg(h->device);
+    if (h->physics == 1) {
+        CUDA_TRY(cudaMemcpyAsync(d_modal, h->B[h->cur], len * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+        return DG_OK;
+    }
     return to_api(h, h->B[h->cur], h->L[h->cur], d_modal, h->href);
 }
 
@@ -647,6 +751,11 @@ dg_status dg_get_state(dg_handle h, double *modal, size_t len)
     if (!modal || len != h->len) return fail(DG_EINVAL, "state length %zu, expected %zu", len, h->len);
     if (!h->have_state) return fail(DG_EINVAL, "no state set");
     DeviceGuard dg(h->device);
+    if (h->physics == 1) {
+        CUDA_TRY(cudaMemcpyAsync(modal, h->B[h->cur], len * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+        CUDA_TRY(cudaStreamSynchronize(h->stream));
+        return DG_OK;
+    }
     if (dg_status s = to_api(h, h->B[h->cur], h->L[h->cur], h->stage64, h->href)) return s;
     CUDA_TRY(cudaMemcpyAsync(modal, h->stage64, len * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     CUDA_TRY(cudaStreamSynchronize(h->stream));
@@ -660,6 +769,21 @@ dg_status dg_rhs(dg_handle h, const double *modal_in, double *tend_out, size_t l
     DeviceGuard dg(h->device);
     // scratch: the increment buffers are free between steps
     void *in = h->I[0], *outb = h->I[1];
+    if (h->physics == 1) {
+        CUDA_TRY(cudaMemcpyAsync(in, modal_in, len * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+        StageArgs<double> a;
+        std::memset(&a, 0, sizeof a);
+        a.status = h->d_status;
+        a.base = static_cast<double *>(in);
+        a.out_rhs = static_cast<double *>(outb);
+        if (launch_plane(h, a))
+            return fail(DG_ECUDA, "planar stage launch failed: %s", cudaGetErrorString(cudaGetLastError()));
+        h->launches++;
+        CUDA_TRY(cudaMemcpyAsync(tend_out, outb, len * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+        CUDA_TRY(cudaStreamSynchronize(h->stream));
+        if (h->check) return read_status(h);
+        return DG_OK;
+    }
     const double href = h->f32() ? mean_depth(modal_in, h->nel, h->nphi) : 0.0;
     CUDA_TRY(cudaMemcpyAsync(h->stage64, modal_in, len * sizeof(double), cudaMemcpyHostToDevice, h->stream));
     if (dg_status s = to_internal(h, h->stage64, in, nullptr, href)) return s;
@@ -800,6 +924,7 @@ extern "C" {
 dg_status dg_total_mass(dg_handle h, double *mass)
 {
     if (dg_status s = check(h)) return s;
+    if (h->physics == 1) return planar_unsupported(h, "dg_total_mass");
     if (!mass) return fail(DG_EINVAL, "mass is NULL");
     if (!h->have_state) return fail(DG_EINVAL, "no state set");
     DeviceGuard dg(h->device);
@@ -814,6 +939,7 @@ dg_status dg_total_mass(dg_handle h, double *mass)
 dg_status dg_total_mass_device(dg_handle h, double *d_mass)
 {
     if (dg_status s = check(h)) return s;
+    if (h->physics == 1) return planar_unsupported(h, "dg_total_mass_device");
     if (!d_mass) return fail(DG_EINVAL, "d_mass is NULL");
     if (!h->have_state) return fail(DG_EINVAL, "no state set");
     DeviceGuard dg(h->device);
@@ -823,6 +949,7 @@ dg_status dg_total_mass_device(dg_handle h, double *d_mass)
 dg_status dg_max_dt(dg_handle h, double cfl, double *dt)
 {
     if (dg_status s = check(h)) return s;
+    if (h->physics == 1) return planar_unsupported(h, "dg_max_dt");
     if (!dt || !(cfl > 0)) return fail(DG_EINVAL, "need cfl > 0 and dt != NULL");
     if (!h->have_state) return fail(DG_EINVAL, "no state set");
     DeviceGuard dg(h->device);
@@ -850,6 +977,7 @@ dg_status dg_max_dt(dg_handle h, double cfl, double *dt)
 dg_status dg_projection_nodes(dg_handle h, double *lam, size_t nlam, double *theta, size_t ntheta)
 {
     if (dg_status s = check(h)) return s;
+    if (h->physics == 1) return planar_unsupported(h, "dg_projection_nodes");
     const int nm = h->tab.nm;
     if (!lam || !theta || nlam != (size_t)h->nlon * nm || ntheta != (size_t)h->nlat * nm)
         return fail(DG_EINVAL, "need nlon*nm = %zu and nlat*nm = %zu values", (size_t)h->nlon * nm,
@@ -865,6 +993,7 @@ dg_status dg_projection_nodes(dg_handle h, double *lam, size_t nlam, double *the
 dg_status dg_project_nodal(dg_handle h, const double *nodal, size_t len_nodal, double *modal_out, size_t len)
 {
     if (dg_status s = check(h)) return s;
+    if (h->physics == 1) return planar_unsupported(h, "dg_project_nodal");
     const int n = h->n, nm = h->tab.nm;
     if (!nodal || !modal_out || len != h->len || len_nodal != h->nel * 3 * nm * nm)
         return fail(DG_EINVAL, "bad lengths");
@@ -919,8 +1048,8 @@ dg_status dg_attach_mlp(dg_handle h, dg_mlp m)
         h->mlp = nullptr;
         return DG_OK;
     }
-    if (h->p != 1 || h->prec != DG_PREC_FP32)
-        return fail(DG_EUNSUPPORTED, "the learned source needs a degree-1 FP32 solver");
+    if (h->physics != 0 || h->p != 1 || h->prec != DG_PREC_FP32)
+        return fail(DG_EUNSUPPORTED, "the learned source needs a degree-1 FP32 sphere solver");
     if (!dg_mlp_shape_is(m, 60, 128, 12)) return fail(DG_EINVAL, "the learned source needs a 60-128-128-12 network");
     if (!h->src && cudaMalloc(&h->src, sizeof(float) * h->len) != cudaSuccess)
         return fail(DG_ENOMEM, "cudaMalloc of the source buffer failed");
@@ -932,6 +1061,7 @@ dg_status dg_restrict_from(dg_handle coarse, dg_handle fine)
 {
     if (dg_status s = check(coarse)) return s;
     if (dg_status s = check(fine)) return s;
+    if (coarse->physics != 0 || fine->physics != 0) return planar_unsupported(coarse, "dg_restrict_from");
     if (!fine->have_state) return fail(DG_EINVAL, "the fine solver has no state");
     if (coarse->device != fine->device) return fail(DG_EINVAL, "the solvers live on different devices");
     const int r = fine->nlon / coarse->nlon;

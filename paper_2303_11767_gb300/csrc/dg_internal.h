@@ -192,6 +192,18 @@ int dg_mlp_launch_source(const dg_mlp_ctx *m, const float *base, const float *in
                          const double *c0, float *src, void *stream);
 bool dg_mlp_shape_is(const dg_mlp_ctx *m, int nin, int h, int nout);
 
+// dg_plane.cu: planar linear advection (one scalar, periodic unit square).
+// k = M^{-1} h(u) with the FP64 stage semantics of StageArgs (href, rows, lo
+// unused); cx = 2 / dx, cy = 2 / dy; alpha_speed 1: Rusanov alpha = |beta|,
+// 0: |beta . n|.
+struct PlaneArgs {
+    StageArgs<double> s;
+    BasisTab<double> basis;
+    double bx, by, cx, cy;
+    int nx, ny, alpha_speed;
+};
+int dg_launch_stage_plane(int n, const PlaneArgs &p, void *stream);
+
 // dg_probe.cu: measured FP64 FMA rate of the current device (GFLOP/s).
 int dg_probe_fp64_gflops(int reps, double *gflops);
 

@@ -33,6 +33,8 @@ SIGNATURES = {
     "dg_set_device": (ctypes.c_int, [ctypes.c_int]),
     "dg_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                  ctypes.c_double, ctypes.POINTER(ctypes.c_void_p)]),
+    "dg_create_plane_advection": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                                 ctypes.c_double, ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)]),
     "dg_destroy": (ctypes.c_int, [_H]),
     "dg_set_option": (ctypes.c_int, [_H, ctypes.c_int, ctypes.c_longlong]),
     "dg_state_len": (ctypes.c_size_t, [_H]),
@@ -166,9 +168,29 @@ class Solver:
         self.nphi = self.n * self.n
         self.nm = self.degree + 9
         self.radius, self.g, self.omega = float(radius), float(g), float(omega)
+        self.nfields = 3
         self.set_option(OPT_PRECISION, PREC[precision] if isinstance(precision, str) else int(precision))
         self.set_option(OPT_RK_ORDER, rk_order)
         self.set_option(OPT_CHECK_FINITE, int(bool(check_finite)))
+
+    @classmethod
+    def plane_advection(cls, nx, ny, degree, bx=1.0, by=1.0, alpha_speed=False, rk_order=4, check_finite=True):
+        """The paper's planar validation problem: du/dt + div(beta u) = 0 on the
+        periodic unit square, FP64; state shape (ny, nx, 1, (p+1)^2)."""
+        self = cls.__new__(cls)
+        h = ctypes.c_void_p()
+        _check(lib().dg_create_plane_advection(int(nx), int(ny), int(degree), float(bx), float(by),
+                                               int(bool(alpha_speed)), ctypes.byref(h)))
+        self._h = h
+        self.nlon, self.nlat, self.degree = int(nx), int(ny), int(degree)
+        self.n = self.degree + 1
+        self.nphi = self.n * self.n
+        self.nm = self.degree + 9
+        self.radius, self.g, self.omega = 1.0, 0.0, 0.0
+        self.nfields = 1
+        self.set_option(OPT_RK_ORDER, rk_order)
+        self.set_option(OPT_CHECK_FINITE, int(bool(check_finite)))
+        return self
 
     # -- lifetime
     def close(self):
@@ -198,7 +220,7 @@ class Solver:
 
     @property
     def shape(self):
-        return (self.nlat, self.nlon, 3, self.nphi)
+        return (self.nlat, self.nlon, self.nfields, self.nphi)
 
     def _host(self, u):
         u = np.ascontiguousarray(u, dtype=np.float64).reshape(-1)
