@@ -68,8 +68,10 @@ constexpr int TC_TPE = 2;
 
 // Shared-memory plan (bytes) of one 4-row tile.  A1 / A1h (GEMM1 operands
 // of the tile and of the halo rows) are dead once GEMM1 has completed, so
-// GEMM2's operand A2 reuses the region; the row exchange buffers XN / XS
-// live in node chunks of A2 that are written only after the exchange.
+// GEMM2's operand A2 reuses the region.  Field h has no source term: its S
+// chunks of A2 are never written and GEMM2 skips them (whole K steps, so CN
+// must be even).  The 16-bit row exchange of the theta faces (XN: N traces,
+// XS: S-face fluxes) lives there when it fits, else in its own region.
 template <int N>
 struct TcSmem {
     using GE = TcGeo<N>;
@@ -82,11 +84,12 @@ struct TcSmem {
     static constexpr uint32_t SZ_A1H = 3 * GE::K1C * CH;
     static constexpr uint32_t SZ_A2 = 3 * GE::KC2 * CH;
     static constexpr uint32_t SZ_A = SZ_A1 + SZ_A1H > SZ_A2 ? SZ_A1 + SZ_A1H : SZ_A2;
-    static constexpr uint32_t BYTES = A + SZ_A;
-    static constexpr uint32_t XN = A;                   // field 0, node chunks
-    static constexpr uint32_t XS = A + GE::KC2 * CH;    // field 1, node chunks
-    static constexpr uint32_t SZ_X = 4 * 32 * 3 * N * 4;
-    static_assert(SZ_X <= 3 * GE::CN * CH, "row exchange exceeds the node chunks");
+    static constexpr bool SKIP_S0 = GE::CN % 2 == 0;
+    static constexpr uint32_t SZ_X = 4 * 32 * 3 * N * 2;   // one 16-bit exchange array
+    static constexpr bool X_IN_S0 = SKIP_S0 && 2 * SZ_X <= GE::CN * CH;
+    static constexpr uint32_t XN = X_IN_S0 ? A + 2 * GE::CN * CH : A + SZ_A;
+    static constexpr uint32_t XS = XN + SZ_X;
+    static constexpr uint32_t BYTES = A + SZ_A + (X_IN_S0 ? 0 : 2 * SZ_X);
     static_assert(3 * GE::N1 + 48 <= (int)TMEM_COLS, "tensor-memory columns");
     static_assert(BYTES <= 113 * 1024, "two CTAs per SM");
 };
@@ -102,6 +105,8 @@ struct Op<__nv_bfloat16> {
         __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
         return *reinterpret_cast<uint32_t *>(&v);
     }
+    __device__ static uint16_t to16(float x) { return __bfloat16_as_ushort(__float2bfloat16_rn(x)); }
+    __device__ static float from16(uint16_t u) { return __bfloat162float(__ushort_as_bfloat16(u)); }
     static uint16_t host_bits(float x)
     {
         __nv_bfloat16 v = __float2bfloat16_rn(x);
@@ -121,6 +126,8 @@ struct Op<__half> {
         __half2 v = __floats2half2_rn(a, b);
         return *reinterpret_cast<uint32_t *>(&v);
     }
+    __device__ static uint16_t to16(float x) { return __half_as_ushort(__float2half_rn(x)); }
+    __device__ static float from16(uint16_t u) { return __half2float(__ushort_as_half(u)); }
     static uint16_t host_bits(float x)
     {
         __half v = __float2half_rn(x);
@@ -207,6 +214,9 @@ __device__ __forceinline__ void tmem_dealloc(uint32_t taddr)
 {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(TMEM_COLS) : "memory");
 }
+
+// Barrier among the 4 warps of one part of the CTA (id 1; id 0 is __syncthreads).
+__device__ __forceinline__ void part_barrier() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
 
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
@@ -378,8 +388,8 @@ __global__ void __launch_bounds__(128 * TC_TPE, 2) tc_stage_kernel(const StageAr
     const uint32_t tl = tbase + ((uint32_t)(32 * q4) << 16);
     unsigned char *const a2row = opA + rowoff;
     auto a2 = [&](int f, int c) { return a2row + (uint32_t)(f * KC2 + c) * CH; };
-    float *XN = reinterpret_cast<float *>(sm + SM::XN);
-    float *XS = reinterpret_cast<float *>(sm + SM::XS);
+    uint16_t *XN = reinterpret_cast<uint16_t *>(sm + SM::XN);
+    uint16_t *XS = reinterpret_cast<uint16_t *>(sm + SM::XS);
 
     // own traces of 3 fields, columns [NC + c0, NC + c0 + 2N): (S, N) for
     // c0 = 0, (W, E) for c0 = 2N; unscaled
@@ -449,9 +459,13 @@ __global__ void __launch_bounds__(128 * TC_TPE, 2) tc_stage_kernel(const StageAr
         }
     }
 
-    // ---- S5 theta faces (part PN) through the row exchange: every element
-    //      evaluates its S edge; its N edge is the S edge of the element
-    //      above (for the top row of a full tile: evaluated against the halo)
+    // ---- S5 theta faces (part PN) through the 16-bit row exchange (the
+    //      faces' fluxes are rounded to the operand type in A2 anyway; the
+    //      neighbour's trace carries one rounding of the operand type): every
+    //      element evaluates its S edge; its N edge is the S edge of the
+    //      element above (for the top row of a full tile: evaluated against
+    //      the halo).  Only part PN's warps meet at these barriers; the other
+    //      part goes on to the Gauss-point fluxes.
     float tsn[3][2 * N];   // [0, N) S, [N, 2N) N
     float halo[3][N];      // row 0: N trace of the row south; row 3: S trace of the row north
     if (part == PN) {
@@ -477,9 +491,10 @@ __global__ void __launch_bounds__(128 * TC_TPE, 2) tc_stage_kernel(const StageAr
 #pragma unroll
         for (int f = 0; f < 3; ++f)
 #pragma unroll
-            for (int k = 0; k < N; ++k) XN[((q4 * 3 + f) * N + k) * 32 + l] = tsn[f][N + k];
+            for (int k = 0; k < N; ++k)
+                XN[((q4 * 3 + f) * N + k) * 32 + l] = Op<OpT>::to16(tsn[f][N + k] * (f == 0 ? 1.0f : MS));
+        part_barrier();
     }
-    __syncthreads();
     float efS[3][N];
     if (part == PN) {
         const float cgs = A.cG * __ldg(&RT->ce_s);
@@ -489,7 +504,8 @@ __global__ void __launch_bounds__(128 * TC_TPE, 2) tc_stage_kernel(const StageAr
             float Sq[3], Nq[3], o[3];
 #pragma unroll
             for (int f = 0; f < 3; ++f) {
-                Sq[f] = q4 > 0 ? XN[(((q4 - 1) * 3 + f) * N + k) * 32 + l] : halo[f][k];
+                Sq[f] = q4 > 0 ? Op<OpT>::from16(XN[(((q4 - 1) * 3 + f) * N + k) * 32 + l]) * (f == 0 ? 1.0f : IMS)
+                               : halo[f][k];
                 Nq[f] = tsn[f][k];
             }
             dgk::rusanov_th(Sq, Nq, href, gg, cgs, o, ss, ga_t);
@@ -500,16 +516,16 @@ __global__ void __launch_bounds__(128 * TC_TPE, 2) tc_stage_kernel(const StageAr
 #pragma unroll
         for (int f = 0; f < 3; ++f)
 #pragma unroll
-            for (int k = 0; k < N; ++k) XS[((q4 * 3 + f) * N + k) * 32 + l] = efS[f][k];
+            for (int k = 0; k < N; ++k) XS[((q4 * 3 + f) * N + k) * 32 + l] = Op<OpT>::to16(efS[f][k]);
+        part_barrier();
     }
-    __syncthreads();
     float efN[3][N];
     if (part == PN) {
         if (q4 + 1 < Wv) {
 #pragma unroll
             for (int f = 0; f < 3; ++f)
 #pragma unroll
-                for (int k = 0; k < N; ++k) efN[f][k] = XS[(((q4 + 1) * 3 + f) * N + k) * 32 + l];
+                for (int k = 0; k < N; ++k) efN[f][k] = Op<OpT>::from16(XS[(((q4 + 1) * 3 + f) * N + k) * 32 + l]);
         } else if (j0 + q4 + 1 >= A.nlat) {
 #pragma unroll
             for (int f = 0; f < 3; ++f)
@@ -533,7 +549,6 @@ __global__ void __launch_bounds__(128 * TC_TPE, 2) tc_stage_kernel(const StageAr
             if (interior) st_int |= sn;
         }
     }
-    __syncthreads();   // the exchange buffers turn back into operand chunks
     if (part == PN) {
 #pragma unroll
         for (int f = 0; f < 3; ++f) {
@@ -599,7 +614,7 @@ __global__ void __launch_bounds__(128 * TC_TPE, 2) tc_stage_kernel(const StageAr
             for (int f = 0; f < 3; ++f) {
                 put_chunk<OpT>(a2(f, g), Fv[f]);
                 put_chunk<OpT>(a2(f, CN + g), Gq[f]);
-                put_chunk<OpT>(a2(f, 2 * CN + g), Sv[f]);
+                if (f > 0 || !SM::SKIP_S0) put_chunk<OpT>(a2(f, 2 * CN + g), Sv[f]);
             }
         }
         if (interior) st_int |= sq;
@@ -615,9 +630,11 @@ __global__ void __launch_bounds__(128 * TC_TPE, 2) tc_stage_kernel(const StageAr
         constexpr uint32_t LB2 = N2 * 16;
         constexpr uint32_t id2 = idesc<Op<OpT>::bf16>(128, N2);
         for (int f = 0; f < 3; ++f)
-            for (int s = 0; s < KC2 / 2; ++s)
+            for (int s = 0; s < KC2 / 2; ++s) {
+                if (f == 0 && SM::SKIP_S0 && 2 * s >= 2 * CN && 2 * s < 3 * CN) continue;   // S_h = 0
                 mma(tbase + (uint32_t)(f * N1), sdesc(a0 + (uint32_t)(f * KC2 + 2 * s) * CH, CH, 128),
                     sdesc(b2 + 2 * s * LB2, LB2, 128), id2, s > 0);
+            }
         mma_commit(mb);
     }
     if (!mbar_wait(mb, 1)) st |= DG_STATUS_TIMEOUT;
