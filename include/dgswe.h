@@ -112,6 +112,16 @@ dg_status dg_create(int nlon, int nlat, int degree, double radius, double g, dou
 dg_status dg_create_plane_advection(int nx, int ny, int degree, double bx, double by, int alpha_speed,
                                     dg_handle *out);
 
+/* Planar shallow water on the f-plane (Sec. 4.3, the geostrophic adjustment
+ * set-up, also the workload of the paper's timings): (h, hu, hv) on the
+ * square [0, L]^2, periodic in both directions, constant Coriolis parameter
+ * f, nx x ny elements of degree 0..4, FP64; F = (hu, hu u + g h^2/2, hu v),
+ * G = (hv, hv u, hv v + g h^2/2), S = (0, f hv, -f hu), Rusanov alpha = the
+ * larger one-sided |u| + c or |v| + c.  State layout as on the sphere,
+ * [y j][x i][field f][mode m]; the same calls as dg_create_plane_advection
+ * plus dg_total_mass (int h dx dy). */
+dg_status dg_create_plane_swe(int nx, int ny, int degree, double L, double g, double f, dg_handle *out);
+
 /* Free the handle and its device buffers.  NULL is accepted. */
 dg_status dg_destroy(dg_handle h);
 

@@ -32,6 +32,9 @@ def lib():
         L.oracle_create_sphere.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                            ctypes.c_double, ctypes.c_double, ctypes.c_double]
         L.oracle_create_plane_advection.restype = ctypes.c_void_p
+        L.oracle_create_plane_swe.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                              ctypes.c_double, ctypes.c_double]
+        L.oracle_create_plane_swe.restype = ctypes.c_void_p
         L.oracle_create_plane_advection.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                                     ctypes.c_double, ctypes.c_double, ctypes.c_int]
         L.oracle_destroy.argtypes = [ctypes.c_void_p]
@@ -131,6 +134,14 @@ class Oracle:
     def plane_advection(cls, nx, ny, p, bx=1.0, by=1.0, alpha_speed=False):
         """alpha_speed: Rusanov alpha = |beta| (True) or |beta . n| (False)."""
         return cls(lib().oracle_create_plane_advection(nx, ny, p, bx, by, int(alpha_speed)), nx, ny, p, 1)
+
+    @classmethod
+    def plane_swe(cls, nx, ny, p, L=1.0e7, g=9.80616, f=1.0e-4):
+        """Shallow water on the f-plane, [0, L]^2 periodic (h, hu, hv)."""
+        h = lib().oracle_create_plane_swe(nx, ny, p, L, g, f)
+        if not h:
+            raise ValueError("invalid planar shallow-water parameters")
+        return cls(h, nx, ny, p, 3)
 
     def __del__(self):
         if getattr(self, "_h", None) and _lib is not None:

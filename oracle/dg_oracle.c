@@ -26,6 +26,7 @@
  *   Table "Butcher" (SSP RK1..RK4)                                -> oracle_rk_step()
  *   Sec. 2, Courant number p c dt / H                             -> oracle_max_dt()
  *   Eq. (lin_adv) planar linear advection (validation problem)    -> flux_advection()
+ *   Sec. 4.3 planar shallow water on the f-plane                  -> flux_plane_swe()
  *
  * Readings where the paper is silent (each one also listed in the design doc):
  *   basis: orthonormal Legendre L_k = sqrt((2k+1)/2) P_k, mode m = b*n + a with
@@ -54,6 +55,7 @@
 
 #define PHYS_SPHERE_SWE 0
 #define PHYS_PLANE_ADVECTION 1
+#define PHYS_PLANE_SWE 2
 
 typedef struct {
     int physics;
@@ -62,6 +64,7 @@ typedef struct {
     int nf;            /* fields: 3 for SWE, 1 for advection */
     int nm;            /* points per direction for mass, projection and norms */
     double R, g, omega;
+    double fcor;       /* planar shallow water: constant Coriolis parameter (f-plane) */
     double bx, by;     /* advection velocity (planar advection only) */
     int alpha_speed;   /* planar advection: 1 -> alpha = |beta|, 0 -> |beta . n| */
     int alpha_global;  /* sphere: 1 -> the wave speeds of every face are the global maxima */
@@ -254,7 +257,7 @@ static oracle_ctx *ctx_alloc(int physics, int nx, int ny, int p)
     c->physics = physics;
     c->nx = nx; c->ny = ny; c->p = p; c->n = p + 1; c->nphi = c->n * c->n;
     c->nm = p + 9;
-    c->nf = physics == PHYS_SPHERE_SWE ? 3 : 1;
+    c->nf = physics == PHYS_PLANE_ADVECTION ? 1 : 3;
     c->nthreads = 1;
     c->xg = malloc(sizeof(double) * c->n); c->wg = malloc(sizeof(double) * c->n);
     c->xm = malloc(sizeof(double) * c->nm); c->wm = malloc(sizeof(double) * c->nm);
@@ -316,6 +319,19 @@ oracle_ctx *oracle_create_sphere(int nlon, int nlat, int p, double R, double g, 
     return c;
 }
 
+/* Planar shallow water on the f-plane, square domain [0, L]^2, periodic in
+ * both directions (the geostrophic adjustment setup of Sec. 4.3). */
+oracle_ctx *oracle_create_plane_swe(int nx, int ny, int p, double L, double g, double f)
+{
+    if (!(L > 0.0) || !(g > 0.0)) return NULL;
+    oracle_ctx *c = ctx_alloc(PHYS_PLANE_SWE, nx, ny, p);
+    if (!c) return NULL;
+    c->g = g; c->fcor = f; c->R = 1.0;
+    c->x0 = 0.0; c->y0 = 0.0; c->dx = L / nx; c->dy = L / ny;
+    if (ctx_build_mass(c)) { oracle_destroy(c); return NULL; }
+    return c;
+}
+
 /* Planar scalar advection du/dt + div(beta u) = 0 (Eq. lin_adv) on the unit
  * square, periodic in both directions.  alpha_speed selects the Rusanov alpha:
  * 1 -> |beta|, 0 -> |beta . n|. */
@@ -363,6 +379,27 @@ static int flux_sphere(const oracle_ctx *c, const double *q, double theta,
     return 1;
 }
 
+/* Planar shallow water on the f-plane (Sec. 4.3, geostrophic adjustment):
+ *   F = (hu, hu u + g h^2/2, hu v),  G = (hv, hv u, hv v + g h^2/2),
+ *   S = (0, f hv, -f hu).  Returns 0 if h <= 0. */
+static int flux_plane_swe(const oracle_ctx *c, const double *q, double *F, double *G, double *S)
+{
+    double h = q[0];
+    if (!(h > 0.0)) return 0;
+    double u = q[1] / h, v = q[2] / h;
+    double pres = 0.5 * c->g * h * h;
+    F[0] = h * u;
+    F[1] = h * u * u + pres;
+    F[2] = h * u * v;
+    G[0] = h * v;
+    G[1] = h * v * u;
+    G[2] = h * v * v + pres;
+    S[0] = 0.0;
+    S[1] = c->fcor * h * v;
+    S[2] = -c->fcor * h * u;
+    return 1;
+}
+
 /* Planar linear advection: F = bx u, G = by u, S = 0. */
 static int flux_advection(const oracle_ctx *c, const double *q, double *F, double *G, double *S)
 {
@@ -375,6 +412,7 @@ static int flux_advection(const oracle_ctx *c, const double *q, double *F, doubl
 static int physical_flux(const oracle_ctx *c, const double *q, double y, double *F, double *G, double *S)
 {
     if (c->physics == PHYS_SPHERE_SWE) return flux_sphere(c, q, y, F, G, S);
+    if (c->physics == PHYS_PLANE_SWE) return flux_plane_swe(c, q, F, G, S);
     return flux_advection(c, q, F, G, S);
 }
 
@@ -391,6 +429,11 @@ static double max_eigenvalue(const oracle_ctx *c, const double *q, double y, int
         double u = q[1] / h, v = q[2] / h, cs = sqrt(c->g * h);
         if (nx != 0) return (fabs(u) + cs) / (c->R * cos(y));
         return (fabs(v) + cs) / c->R;
+    }
+    if (c->physics == PHYS_PLANE_SWE) {   /* eigenvalues u, u +- c (x) and v, v +- c (y) */
+        double h = q[0];
+        double u = q[1] / h, v = q[2] / h, cs = sqrt(c->g * h);
+        return nx != 0 ? fabs(u) + cs : fabs(v) + cs;
     }
     if (c->alpha_speed) return sqrt(c->bx * c->bx + c->by * c->by);
     return fabs(c->bx * nx + c->by * ny);

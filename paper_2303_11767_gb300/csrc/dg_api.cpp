@@ -67,7 +67,7 @@ unsigned long long g_basis_uploaded = 0;   // per-device bit: constant tables pr
 }  // namespace
 
 struct dg_ctx {
-    int physics = 0;   // 0: shallow water on the sphere; 1: planar linear advection (one scalar)
+    int physics = 0;   // 0: shallow water on the sphere; 1: planar linear advection; 2: planar shallow water
     int nlon = 0, nlat = 0, p = 0, n = 0, nphi = 0;
     size_t nel = 0, len = 0;
     double R = 0, g = 0, omega = 0;
@@ -104,6 +104,7 @@ struct dg_ctx {
     float *src = nullptr;         // its per-stage modal output
     std::vector<GraphEntry> graphs;
     double bx = 0, by = 0;       // planar advection velocity
+    double plen = 1.0, fcor = 0; // planar domain side and f-plane Coriolis parameter
     int alpha_speed = 0;         // planar: Rusanov alpha = |beta| (1) or |beta . n| (0)
     BasisTab<double> pbasis{};   // planar: basis tables of degree p
     bool f32() const { return prec != DG_PREC_FP64; }                 // FP32 storage
@@ -221,18 +222,21 @@ int launch_plane(dg_ctx *h, const StageArgs<double> &a)
     pa.basis = h->pbasis;
     pa.bx = h->bx;
     pa.by = h->by;
-    pa.cx = 2.0 * h->nlon;   // 2 / dx on the unit square
-    pa.cy = 2.0 * h->nlat;
+    pa.cx = 2.0 * h->nlon / h->plen;   // 2 / dx on the square of side plen
+    pa.cy = 2.0 * h->nlat / h->plen;
     pa.nx = h->nlon;
     pa.ny = h->nlat;
     pa.alpha_speed = h->alpha_speed;
+    pa.swe = h->physics == 2;
+    pa.g = h->g;
+    pa.fcor = h->fcor;
     return dg_launch_stage_plane(h->n, pa, h->stream);
 }
 
 dg_status planar_unsupported(dg_ctx *h, const char *what)
 {
     (void)h;
-    return fail(DG_EUNSUPPORTED, "%s is not available for planar advection", what);
+    return fail(DG_EUNSUPPORTED, "%s is not available for the planar problems", what);
 }
 
 // Global Rusanov mode: the stage input's two speeds into h->galpha, then the
@@ -291,7 +295,7 @@ dg_status launch_step_t(dg_ctx *h, double dt, int cur, const RowTab<T> *rows)
             r = h->tc() ? dg_launch_stage_tc(h->n, h->prec - DG_PREC_FP32_TC_BF16, a, h->stream)
                         : dg_launch_stage<T>(h->n, a, h->stream);
         } else {
-            r = h->physics == 1 ? launch_plane(h, a) : dg_launch_stage<T>(h->n, a, h->stream);
+            r = h->physics != 0 ? launch_plane(h, a) : dg_launch_stage<T>(h->n, a, h->stream);
         }
         if (r) return fail(DG_ECUDA, "stage kernel launch failed: %s", cudaGetErrorString(cudaGetLastError()));
         h->launches++;
@@ -524,6 +528,29 @@ dg_status dg_create(int nlon, int nlat, int degree, double radius, double g, dou
     return DG_OK;
 }
 
+dg_status dg_create_plane_swe(int nx, int ny, int degree, double L, double g, double f, dg_handle *out)
+{
+    if (!(L > 0) || !(g > 0) || !std::isfinite(f) || !std::isfinite(L))
+        return fail(DG_EINVAL, "need L > 0, g > 0 and a finite f");
+    dg_status st = dg_create_plane_advection(nx, ny, degree, 0.0, 0.0, 0, out);
+    if (st) return st;
+    dg_ctx *h = *out;
+    DeviceGuard dg(h->device);
+    // three fields: re-size the state buffers
+    free_state_buffers(h);
+    h->physics = 2;
+    h->len = h->nel * 3 * h->nphi;
+    h->plen = L;
+    h->g = g;
+    h->fcor = f;
+    if ((st = alloc_state_buffers(h)) != DG_OK) {
+        dg_destroy(h);
+        *out = nullptr;
+        return st;
+    }
+    return DG_OK;
+}
+
 dg_status dg_create_plane_advection(int nx, int ny, int degree, double bx, double by, int alpha_speed,
                                     dg_handle *out)
 {
@@ -561,6 +588,9 @@ dg_status dg_create_plane_advection(int nx, int ny, int degree, double bx, doubl
         }
         h->pbasis = t.basis;
         dg_free_tables(t);
+        h->tab.n = h->n;
+        h->tab.nm = degree + 9;
+        dg_gauss_legendre(h->tab.nm, h->tab.xm, h->tab.wm);
     }
     dg_status st = DG_OK;
     if (cudaStreamCreateWithFlags(&h->own_stream, cudaStreamNonBlocking) != cudaSuccess) {
@@ -614,7 +644,7 @@ dg_status dg_set_option(dg_handle h, int key, long long value)
 {
     if (dg_status s = check(h)) return s;
     DeviceGuard dg(h->device);
-    if (h->physics == 1 && ((key == DG_OPT_PRECISION && value != DG_PREC_FP64) || (key == DG_OPT_ALPHA_MODE && value)))
+    if (h->physics != 0 && ((key == DG_OPT_PRECISION && value != DG_PREC_FP64) || (key == DG_OPT_ALPHA_MODE && value)))
         return planar_unsupported(h, key == DG_OPT_PRECISION ? "a precision other than FP64" : "the global alpha mode");
     switch (key) {
     case DG_OPT_PRECISION: {
@@ -686,7 +716,7 @@ dg_status dg_set_state_device(dg_handle h, const double *d_modal, size_t len)
     if (dg_status s = check(h)) return s;
     if (!d_modal || len != h->len) return fail(DG_EINVAL, "state length %zu, expected %zu", len, h->len);
     DeviceGuard dg(h->device);
-    if (h->physics == 1) {
+    if (h->physics != 0) {
         CUDA_TRY(cudaMemcpyAsync(h->B[0], d_modal, len * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
         h->cur = 0;
         h->href = 0.0;
@@ -715,7 +745,7 @@ dg_status dg_set_state(dg_handle h, const double *modal, size_t len)
     if (dg_status s = check(h)) return s;
     if (!modal || len != h->len) return fail(DG_EINVAL, "state length %zu, expected %zu", len, h->len);
     DeviceGuard dg(h->device);
-    if (h->physics == 1) {
+    if (h->physics != 0) {
         CUDA_TRY(cudaMemcpyAsync(h->B[0], modal, len * sizeof(double), cudaMemcpyHostToDevice, h->stream));
         CUDA_TRY(cudaStreamSynchronize(h->stream));
         h->cur = 0;
@@ -738,7 +768,7 @@ dg_status dg_get_state_device(dg_handle h, double *d_modal, size_t len)
     if (!d_modal || len != h->len) return fail(DG_EINVAL, "state length %zu, expected %zu", len, h->len);
     if (!h->have_state) return fail(DG_EINVAL, "no state set");
     DeviceGuard dg(h->device);
-    if (h->physics == 1) {
+    if (h->physics != 0) {
         CUDA_TRY(cudaMemcpyAsync(d_modal, h->B[h->cur], len * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
         return DG_OK;
     }
@@ -751,7 +781,7 @@ dg_status dg_get_state(dg_handle h, double *modal, size_t len)
     if (!modal || len != h->len) return fail(DG_EINVAL, "state length %zu, expected %zu", len, h->len);
     if (!h->have_state) return fail(DG_EINVAL, "no state set");
     DeviceGuard dg(h->device);
-    if (h->physics == 1) {
+    if (h->physics != 0) {
         CUDA_TRY(cudaMemcpyAsync(modal, h->B[h->cur], len * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
         CUDA_TRY(cudaStreamSynchronize(h->stream));
         return DG_OK;
@@ -769,7 +799,7 @@ dg_status dg_rhs(dg_handle h, const double *modal_in, double *tend_out, size_t l
     DeviceGuard dg(h->device);
     // scratch: the increment buffers are free between steps
     void *in = h->I[0], *outb = h->I[1];
-    if (h->physics == 1) {
+    if (h->physics != 0) {
         CUDA_TRY(cudaMemcpyAsync(in, modal_in, len * sizeof(double), cudaMemcpyHostToDevice, h->stream));
         StageArgs<double> a;
         std::memset(&a, 0, sizeof a);
@@ -925,6 +955,23 @@ dg_status dg_total_mass(dg_handle h, double *mass)
 {
     if (dg_status s = check(h)) return s;
     if (h->physics == 1) return planar_unsupported(h, "dg_total_mass");
+    if (h->physics == 2) {   // planar shallow water: R^0 sum_k (dx dy / 2) h_00, compensated, on the host
+        if (!h->have_state) return fail(DG_EINVAL, "no state set");
+        DeviceGuard dg(h->device);
+        std::vector<double> u(h->len);
+        CUDA_TRY(cudaMemcpyAsync(u.data(), h->B[h->cur], h->len * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+        CUDA_TRY(cudaStreamSynchronize(h->stream));
+        const double w = 0.5 * (h->plen / h->nlon) * (h->plen / h->nlat);   // int L0(xi) L0(eta) = 2, jac dx dy / 4
+        double sum = 0.0, comp = 0.0;
+        for (size_t e = 0; e < h->nel; ++e) {
+            const double x = w * u[e * 3 * h->nphi];
+            const double t = sum + x;
+            comp += std::fabs(sum) >= std::fabs(x) ? (sum - t) + x : (x - t) + sum;
+            sum = t;
+        }
+        *mass = sum + comp;
+        return DG_OK;
+    }
     if (!mass) return fail(DG_EINVAL, "mass is NULL");
     if (!h->have_state) return fail(DG_EINVAL, "no state set");
     DeviceGuard dg(h->device);
@@ -939,7 +986,7 @@ dg_status dg_total_mass(dg_handle h, double *mass)
 dg_status dg_total_mass_device(dg_handle h, double *d_mass)
 {
     if (dg_status s = check(h)) return s;
-    if (h->physics == 1) return planar_unsupported(h, "dg_total_mass_device");
+    if (h->physics != 0) return planar_unsupported(h, "dg_total_mass_device");
     if (!d_mass) return fail(DG_EINVAL, "d_mass is NULL");
     if (!h->have_state) return fail(DG_EINVAL, "no state set");
     DeviceGuard dg(h->device);
@@ -949,7 +996,7 @@ dg_status dg_total_mass_device(dg_handle h, double *d_mass)
 dg_status dg_max_dt(dg_handle h, double cfl, double *dt)
 {
     if (dg_status s = check(h)) return s;
-    if (h->physics == 1) return planar_unsupported(h, "dg_max_dt");
+    if (h->physics != 0) return planar_unsupported(h, "dg_max_dt");
     if (!dt || !(cfl > 0)) return fail(DG_EINVAL, "need cfl > 0 and dt != NULL");
     if (!h->have_state) return fail(DG_EINVAL, "no state set");
     DeviceGuard dg(h->device);
@@ -977,8 +1024,18 @@ dg_status dg_max_dt(dg_handle h, double cfl, double *dt)
 dg_status dg_projection_nodes(dg_handle h, double *lam, size_t nlam, double *theta, size_t ntheta)
 {
     if (dg_status s = check(h)) return s;
-    if (h->physics == 1) return planar_unsupported(h, "dg_projection_nodes");
     const int nm = h->tab.nm;
+    if (h->physics != 0) {   // planar: x_i = (i + (1 + x_q) / 2) dx, y likewise, on [0, plen]^2
+        if (!lam || !theta || nlam != (size_t)h->nlon * nm || ntheta != (size_t)h->nlat * nm)
+            return fail(DG_EINVAL, "need nx*nm = %zu and ny*nm = %zu values", (size_t)h->nlon * nm,
+                        (size_t)h->nlat * nm);
+        const double dx = h->plen / h->nlon, dy = h->plen / h->nlat;
+        for (int i = 0; i < h->nlon; ++i)
+            for (int q = 0; q < nm; ++q) lam[(size_t)i * nm + q] = (i + 0.5 * (1.0 + h->tab.xm[q])) * dx;
+        for (int j = 0; j < h->nlat; ++j)
+            for (int q = 0; q < nm; ++q) theta[(size_t)j * nm + q] = (j + 0.5 * (1.0 + h->tab.xm[q])) * dy;
+        return DG_OK;
+    }
     if (!lam || !theta || nlam != (size_t)h->nlon * nm || ntheta != (size_t)h->nlat * nm)
         return fail(DG_EINVAL, "need nlon*nm = %zu and nlat*nm = %zu values", (size_t)h->nlon * nm,
                     (size_t)h->nlat * nm);
@@ -993,8 +1050,31 @@ dg_status dg_projection_nodes(dg_handle h, double *lam, size_t nlam, double *the
 dg_status dg_project_nodal(dg_handle h, const double *nodal, size_t len_nodal, double *modal_out, size_t len)
 {
     if (dg_status s = check(h)) return s;
-    if (h->physics == 1) return planar_unsupported(h, "dg_project_nodal");
     const int n = h->n, nm = h->tab.nm;
+    if (h->physics != 0) {   // planar: the mass matrix is (dx dy / 4) I, so u_m = sum_q w w f L_a L_b
+        const int nf = h->physics == 2 ? 3 : 1;
+        if (!nodal || !modal_out || len != h->len || len_nodal != h->nel * nf * nm * nm)
+            return fail(DG_EINVAL, "bad lengths");
+        std::vector<double> PL((size_t)n * nm);
+        for (int a = 0; a < n; ++a)
+            for (int q = 0; q < nm; ++q) PL[(size_t)a * nm + q] = h->tab.wm[q] * dg_legendre(a, h->tab.xm[q]);
+        for (size_t el = 0; el < h->nel; ++el)
+            for (int f = 0; f < nf; ++f) {
+                const double *v = nodal + (el * nf + f) * nm * nm;
+                double *o = modal_out + (el * nf + f) * h->nphi;
+                for (int b = 0; b < n; ++b)
+                    for (int a = 0; a < n; ++a) {
+                        double acc = 0.0;
+                        for (int qy = 0; qy < nm; ++qy) {
+                            double t = 0.0;
+                            for (int qx = 0; qx < nm; ++qx) t += PL[(size_t)a * nm + qx] * v[qy * nm + qx];
+                            acc += PL[(size_t)b * nm + qy] * t;
+                        }
+                        o[b * n + a] = acc;
+                    }
+            }
+        return DG_OK;
+    }
     if (!nodal || !modal_out || len != h->len || len_nodal != h->nel * 3 * nm * nm)
         return fail(DG_EINVAL, "bad lengths");
     // separable projection: sum over the lambda points, then the theta points

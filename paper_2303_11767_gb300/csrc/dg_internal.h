@@ -192,7 +192,8 @@ int dg_mlp_launch_source(const dg_mlp_ctx *m, const float *base, const float *in
                          const double *c0, float *src, void *stream);
 bool dg_mlp_shape_is(const dg_mlp_ctx *m, int nin, int h, int nout);
 
-// dg_plane.cu: planar linear advection (one scalar, periodic unit square).
+// dg_plane.cu: planar linear advection (one scalar, periodic unit square)
+// and planar shallow water on the f-plane (h, hu, hv; periodic square).
 // k = M^{-1} h(u) with the FP64 stage semantics of StageArgs (href, rows, lo
 // unused); cx = 2 / dx, cy = 2 / dy; alpha_speed 1: Rusanov alpha = |beta|,
 // 0: |beta . n|.
@@ -201,6 +202,8 @@ struct PlaneArgs {
     BasisTab<double> basis;
     double bx, by, cx, cy;
     int nx, ny, alpha_speed;
+    int swe;          // 1: shallow water on the f-plane (3 fields) instead of advection
+    double g, fcor;   // gravity and the constant Coriolis parameter (swe)
 };
 int dg_launch_stage_plane(int n, const PlaneArgs &p, void *stream);
 

@@ -35,6 +35,8 @@ SIGNATURES = {
                                  ctypes.c_double, ctypes.POINTER(ctypes.c_void_p)]),
     "dg_create_plane_advection": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                                  ctypes.c_double, ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)]),
+    "dg_create_plane_swe": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                           ctypes.c_double, ctypes.c_double, ctypes.POINTER(ctypes.c_void_p)]),
     "dg_destroy": (ctypes.c_int, [_H]),
     "dg_set_option": (ctypes.c_int, [_H, ctypes.c_int, ctypes.c_longlong]),
     "dg_state_len": (ctypes.c_size_t, [_H]),
@@ -192,6 +194,25 @@ class Solver:
         self.set_option(OPT_CHECK_FINITE, int(bool(check_finite)))
         return self
 
+    @classmethod
+    def plane_swe(cls, nx, ny, degree, L=1.0e7, g=GRAVITY, f=1.0e-4, rk_order=4, check_finite=True):
+        """Shallow water on the f-plane, [0, L]^2 periodic, FP64; state shape
+        (ny, nx, 3, (p+1)^2)."""
+        self = cls.__new__(cls)
+        h = ctypes.c_void_p()
+        _check(lib().dg_create_plane_swe(int(nx), int(ny), int(degree), float(L), float(g), float(f),
+                                         ctypes.byref(h)))
+        self._h = h
+        self.nlon, self.nlat, self.degree = int(nx), int(ny), int(degree)
+        self.n = self.degree + 1
+        self.nphi = self.n * self.n
+        self.nm = self.degree + 9
+        self.radius, self.g, self.omega = 1.0, float(g), 0.0
+        self.nfields = 3
+        self.set_option(OPT_RK_ORDER, rk_order)
+        self.set_option(OPT_CHECK_FINITE, int(bool(check_finite)))
+        return self
+
     # -- lifetime
     def close(self):
         if getattr(self, "_h", None):
@@ -306,11 +327,12 @@ class Solver:
 
     def project_grid(self, fn_grid):
         """Project fields given on the tensor grid of projection nodes:
-        fn_grid(lam1, th1) -> 3 arrays shaped [len(th1), len(lam1)]."""
+        fn_grid(lam1, th1) -> arrays shaped [len(th1), len(lam1)], one per
+        field (on the planar problems lam1, th1 are the x and y nodes)."""
         lam, th = self.projection_nodes()
         nm = self.nm
         vals = [np.asarray(v, dtype=np.float64).reshape(self.nlat, nm, self.nlon, nm).transpose(0, 2, 1, 3)
-                for v in fn_grid(lam, th)]
+                for v in fn_grid(lam, th)][:self.nfields]
         return self.project_nodal(np.ascontiguousarray(np.stack(vals, axis=2)))
 
 

@@ -182,6 +182,21 @@ class SmoothField:
         return h, h * u, h * v
 
 
+def geostrophic_adjustment_grid(L=1.0e7, h0=1000.0, h1=5.0, sigma_frac=1.0 / 20.0):
+    """Initial fields of the planar geostrophic adjustment set-up of the paper
+    (Sec. 4.3): a Gaussian hump h0 + h1 exp(-r^2 / (2 sigma^2)) centred in
+    [0, L]^2 with sigma = L sigma_frac, fluid at rest.  Returns fn(x1, y1) ->
+    (h, hu, hv) on the tensor grid y1 x x1."""
+    sigma = sigma_frac * L
+
+    def fn(x1, y1):
+        x, y = np.meshgrid(np.asarray(x1), np.asarray(y1))
+        h = h0 + h1 * np.exp(-((x - L / 2) ** 2 + (y - L / 2) ** 2) / (2 * sigma * sigma))
+        return h, np.zeros_like(h), np.zeros_like(h)
+
+    return fn
+
+
 CONFIG_SEEDS = {"c1": 1, "c2": 2, "c3": 3}
 
 

@@ -8,7 +8,7 @@ import numpy as np
 import pytest
 
 import oracle as O
-from paper_2303_11767_gb300 import dgswe
+from paper_2303_11767_gb300 import dgswe, synth
 
 pytestmark = pytest.mark.gpu
 
@@ -87,3 +87,64 @@ def test_planar_sphere_only_calls_are_rejected():
             with pytest.raises(dgswe.DGError) as e:
                 call()
             assert e.value.status == dgswe.DG_EUNSUPPORTED
+
+
+# ------------------------------------------------ shallow water on the f-plane --
+
+L_DOM, G_PL, F_PL = 1.0e7, 9.80616, 1.0e-4
+
+
+@pytest.mark.parametrize("p,nx,ny", [(0, 6, 5), (1, 7, 4), (2, 5, 6), (3, 4, 5), (4, 3, 4)])
+def test_plane_swe_rhs_and_steps_match_oracle(p, nx, ny):
+    o = O.Oracle.plane_swe(nx, ny, p, L_DOM, G_PL, F_PL)
+    rng = np.random.default_rng(10 + p)
+    u = np.zeros(o.shape)
+    u[..., 0, 0] = 2.0 * 1000.0
+    u[..., :, 1:] = rng.normal(size=u[..., :, 1:].shape) * np.array([5.0, 200.0, 200.0])[:, None]
+    u[..., 1:, 0] = rng.normal(size=u[..., 1:, 0].shape) * 500.0
+    want = o.rhs(u)
+    S = o.rhs_magnitude(u)
+    with dgswe.Solver.plane_swe(nx, ny, p, L_DOM, G_PL, F_PL) as s:
+        k = s.rhs(u)
+        for f in range(3):
+            assert np.abs(k[..., f, :] - want[..., f, :]).max() <= 1e-12 * S[..., f, :].max()
+        s.set_option(dgswe.OPT_STEPS_PER_GRAPH, 4)
+        s.set_state(u)
+        m0 = s.total_mass()
+        s.step(10, 100.0)
+        got = s.get_state()
+        m1 = s.total_mass()
+    ref = o.step(u, 10, 100.0, 4)
+    for f in range(3):
+        assert np.abs(got[..., f, :] - ref[..., f, :]).max() <= 1e-12 * np.abs(ref[..., f, :]).max()
+    assert m0 == pytest.approx(o.total_mass(u), rel=1e-14)
+    assert abs(m1 / m0 - 1) < 1e-14
+
+
+def test_geostrophic_adjustment_run_matches_oracle():
+    """The paper's set-up (Sec. 4.3): 50x50 elements, degree 3, RK4, dt = 100 s,
+    T = 36000 s, Gaussian hump on a fluid at rest, f = 1e-4; the initial state
+    is projected by the library and by the oracle, and both runs agree."""
+    nx = ny = 50
+    p = 3
+    o = O.Oracle.plane_swe(nx, ny, p, L_DOM, G_PL, F_PL)
+    o.set_threads(os.cpu_count() or 1)
+    fn = synth.geostrophic_adjustment_grid(L_DOM)
+
+    with dgswe.Solver.plane_swe(nx, ny, p, L_DOM, G_PL, F_PL) as s:
+        u0 = s.project_grid(fn)
+        want0 = o.project_fn(lambda xx, yy: [1000.0 + 5.0 * np.exp(-((xx - L_DOM / 2) ** 2 + (yy - L_DOM / 2) ** 2)
+                                                                   / (2 * (L_DOM / 20) ** 2)), 0 * xx, 0 * xx])
+        np.testing.assert_allclose(u0, want0, rtol=0, atol=1e-12 * np.abs(want0).max())
+        s.set_option(dgswe.OPT_STEPS_PER_GRAPH, 120)
+        s.set_state(u0)
+        m0 = s.total_mass()
+        s.step(360, 100.0)
+        got = s.get_state()
+        m1 = s.total_mass()
+    want = o.step(u0, 360, 100.0, 4)
+    for f in range(3):
+        assert np.abs(got[..., f, :] - want[..., f, :]).max() <= 1e-11 * np.abs(want[..., f, :]).max(), f
+    assert abs(m1 / m0 - 1) < 1e-13
+    # the hump has adjusted: flow in geostrophic rotation, mass unchanged
+    assert np.abs(got[..., 1:, :]).max() > 1.0
