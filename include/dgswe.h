@@ -219,6 +219,15 @@ dg_status dg_mlp_set_params(dg_mlp m, const float *params, size_t n);
  * (t - out_mean) / out_std (host arrays of n_in and n_out values, std > 0). */
 dg_status dg_mlp_set_normalization(dg_mlp m, const float *in_mean, const float *in_std, const float *out_mean,
                                    const float *out_std);
+/* Optional per-latitude-row output statistics for the learned source
+ * (dg_attach_mlp): with them the source of an element of row j is
+ * y * out_std_rows[j][q] + out_mean_rows[j][q] (host arrays of nlat x n_out
+ * values, std > 0) instead of the global out_mean / out_std, so a network
+ * trained on row-normalised targets carries the latitude dependence of the
+ * coarse mesh's error without a position input.  nlat must equal the
+ * attached solver's nlat (else its steps fail with DG_EINVAL); nlat = 0
+ * removes them. */
+dg_status dg_mlp_set_row_normalization(dg_mlp m, int nlat, const float *out_mean_rows, const float *out_std_rows);
 /* Normalised network output of a batch (device arrays). */
 dg_status dg_mlp_forward(dg_mlp m, const float *d_x, int batch, float *d_y);
 /* Mean squared error on normalised targets and its gradient (host buffer of

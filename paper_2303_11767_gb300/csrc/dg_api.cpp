@@ -281,9 +281,11 @@ dg_status launch_step_t(dg_ctx *h, double dt, int cur, const RowTab<T> *rows)
         a.dt = (T)dt;
         if constexpr (sizeof(T) == sizeof(float)) {
             if (h->mlp) {
-                if (dg_mlp_launch_source(h->mlp, reinterpret_cast<const float *>(a.base),
-                                         reinterpret_cast<const float *>(a.inc), (float)h->href, h->nlon, h->nlat,
-                                         h->c0, h->src, h->stream))
+                const int ms = dg_mlp_launch_source(h->mlp, reinterpret_cast<const float *>(a.base),
+                                                    reinterpret_cast<const float *>(a.inc), (float)h->href, h->nlon,
+                                                    h->nlat, h->c0, h->src, h->stream);
+                if (ms == 2) return fail(DG_EINVAL, "the network's row statistics belong to another mesh");
+                if (ms)
                     return fail(DG_ECUDA, "learned source launch failed: %s", cudaGetErrorString(cudaGetLastError()));
                 a.src = reinterpret_cast<const T *>(h->src);
                 h->aux_launches += 2;
@@ -843,8 +845,10 @@ dg_status dg_rhs(dg_handle h, const double *modal_in, double *tend_out, size_t l
         a.base = static_cast<float *>(in);
         a.out_rhs = static_cast<float *>(outb);
         if (h->mlp) {   // the attached learned source is part of the tendency
-            if (dg_mlp_launch_source(h->mlp, a.base, nullptr, (float)href, h->nlon, h->nlat, h->c0, h->src, h->stream))
-                return fail(DG_ECUDA, "learned source launch failed: %s", cudaGetErrorString(cudaGetLastError()));
+            const int ms = dg_mlp_launch_source(h->mlp, a.base, nullptr, (float)href, h->nlon, h->nlat, h->c0, h->src,
+                                                h->stream);
+            if (ms == 2) return fail(DG_EINVAL, "the network's row statistics belong to another mesh");
+            if (ms) return fail(DG_ECUDA, "learned source launch failed: %s", cudaGetErrorString(cudaGetLastError()));
             a.src = h->src;
         }
         if (dg_status gs = enqueue_global_speeds<float>(h, a)) return gs;

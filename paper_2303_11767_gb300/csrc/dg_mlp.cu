@@ -226,6 +226,8 @@ struct dg_mlp_ctx {
     float *w = nullptr, *g = nullptr, *m = nullptr, *v = nullptr;
     __nv_bfloat16 *wb = nullptr;
     float *norm = nullptr;    // in_mean[nin], in_std[nin], out_mean[nout], out_std[nout]
+    float *rownorm = nullptr; // optional per latitude row: out_mean[nlat][nout], out_std[nlat][nout]
+    int rownorm_nlat = 0;
     float *Z1 = nullptr, *A1 = nullptr, *Z2 = nullptr, *A2 = nullptr, *Y = nullptr, *dY = nullptr, *dA = nullptr,
           *dA2 = nullptr, *part = nullptr;
     double *lpart = nullptr;
@@ -237,7 +239,8 @@ namespace {
 
 void free_mlp(dg_mlp_ctx *c)
 {
-    for (float *p : {c->w, c->g, c->m, c->v, c->norm, c->Z1, c->A1, c->Z2, c->A2, c->Y, c->dY, c->dA, c->dA2, c->part})
+    for (float *p : {c->w, c->g, c->m, c->v, c->norm, c->rownorm, c->Z1, c->A1, c->Z2, c->A2, c->Y, c->dY, c->dA, c->dA2,
+                     c->part})
         cudaFree(p);
     cudaFree(c->wb);
     cudaFree(c->lpart);
@@ -449,6 +452,30 @@ dg_status dg_mlp_set_normalization(dg_mlp m, const float *in_mean, const float *
     return DG_OK;
 }
 
+dg_status dg_mlp_set_row_normalization(dg_mlp m, int nlat, const float *out_mean_rows, const float *out_std_rows)
+{
+    if (!m) return mfail(DG_EINVAL, "NULL network");
+    if (nlat == 0) {
+        cudaFree(m->rownorm);
+        m->rownorm = nullptr;
+        m->rownorm_nlat = 0;
+        return DG_OK;
+    }
+    if (nlat < 0 || !out_mean_rows || !out_std_rows) return mfail(DG_EINVAL, "need nlat > 0 and both arrays");
+    const size_t k = (size_t)nlat * m->nout;
+    for (size_t i = 0; i < k; ++i)
+        if (!(out_std_rows[i] > 0)) return mfail(DG_EINVAL, "row std %zu must be positive", i);
+    std::vector<float> n(2 * k);
+    std::memcpy(n.data(), out_mean_rows, sizeof(float) * k);
+    std::memcpy(n.data() + k, out_std_rows, sizeof(float) * k);
+    cudaFree(m->rownorm);
+    m->rownorm = nullptr;
+    MCUDA(cudaMalloc(&m->rownorm, sizeof(float) * n.size()));
+    MCUDA(cudaMemcpy(m->rownorm, n.data(), sizeof(float) * n.size(), cudaMemcpyHostToDevice));
+    m->rownorm_nlat = nlat;
+    return DG_OK;
+}
+
 dg_status dg_mlp_forward(dg_mlp m, const float *d_x, int batch, float *d_y)
 {
     if (!m || !d_x || !d_y || batch < 1 || batch > MAXB) return mfail(DG_EINVAL, "batch must be 1..%d", MAXB);
@@ -500,7 +527,8 @@ namespace {
 __global__ void mlp_source_kernel(const float *__restrict__ base, const float *__restrict__ inc, float href, int nlon,
                                   int nlat, const __nv_bfloat16 *__restrict__ wb, const float *__restrict__ wf,
                                   size_t ob1, size_t oW2, size_t ob2, size_t oW3, size_t ob3,
-                                  const float *__restrict__ norm, float *__restrict__ src)
+                                  const float *__restrict__ norm, const float *__restrict__ rownorm,
+                                  float *__restrict__ src)
 {
     constexpr int NIN = 60, H = 128, NOUT = 12, PER = 12;
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
@@ -537,8 +565,11 @@ __global__ void mlp_source_kernel(const float *__restrict__ base, const float *_
 #pragma unroll
         for (int q = 0; q < NOUT; ++q) y[q] = fmaf(__bfloat162float(wb[oW3 + (size_t)q * H + o]), a2, y[q]);
     }
+    // denormalise: per latitude row if row statistics are set, else globally
+    const float *om = rownorm ? rownorm + (size_t)j * NOUT : norm + 2 * NIN;
+    const float *os = rownorm ? rownorm + (size_t)(nlat + j) * NOUT : norm + 2 * NIN + NOUT;
 #pragma unroll
-    for (int q = 0; q < NOUT; ++q) src[(size_t)e * PER + q] = y[q] * norm[2 * NIN + NOUT + q] + norm[2 * NIN + q];
+    for (int q = 0; q < NOUT; ++q) src[(size_t)e * PER + q] = y[q] * os[q] + om[q];
 }
 
 // Keep the total mass: remove from mode (a=0, b=0) of h the mass the learned
@@ -575,8 +606,9 @@ int dg_mlp_launch_source(const dg_mlp_ctx *m, const float *base, const float *in
 {
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const int nel = nlon * nlat;
+    if (m->rownorm && m->rownorm_nlat != nlat) return 2;   // row statistics of another mesh
     mlp_source_kernel<<<(nel + 63) / 64, 64, 0, s>>>(base, inc, href, nlon, nlat, m->wb, m->w, m->ob1, m->oW2, m->ob2,
-                                                     m->oW3, m->ob3, m->norm, src);
+                                                     m->oW3, m->ob3, m->norm, m->rownorm, src);
     mlp_massfix_kernel<<<1, 256, 0, s>>>(src, c0, nlon, nlat);
     return cudaPeekAtLastError() == cudaSuccess ? 0 : 1;
 }

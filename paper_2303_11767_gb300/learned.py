@@ -103,12 +103,33 @@ def generate(n_pairs, seeds, spinup_s=1800.0, stride=4, target_steps=1, log=prin
     return np.concatenate(X).astype(np.float32), np.concatenate(T).astype(np.float32)
 
 
-def train(X, T, epochs=8, batch=4096, lr=1e-3, seed=0, log=print):
+def row_statistics(T, nlon, nlat):
+    """Per latitude row mean and std of the targets [n_samples, 12] (samples
+    are whole coarse meshes in element order); stds floored at 1e-6 of the
+    output's largest row std."""
+    rows = (np.arange(T.shape[0]) % (nlon * nlat)) // nlon
+    om = np.stack([T[rows == j].mean(0) for j in range(nlat)])
+    sd = np.stack([T[rows == j].std(0) for j in range(nlat)])
+    sd = np.maximum(sd, 1e-6 * sd.max(axis=0, keepdims=True) + 1e-30)
+    return rows, om.astype(np.float32), sd.astype(np.float32)
+
+
+def train(X, T, epochs=8, batch=4096, lr=1e-3, seed=0, log=print, row_norm=False):
+    """row_norm: targets normalised per latitude row (the coarse mesh's error
+    depends on latitude, which the 60 inputs do not carry); the library then
+    denormalises the network output with the row statistics."""
     import torch
 
     mlp = dgswe.MLP(60, 128, 12, seed=seed)
     in_mean, in_std = X.mean(0), X.std(0) + 1e-12
-    out_mean, out_std = T.mean(0), T.std(0) + 1e-30
+    rowstats = None
+    if row_norm:
+        rows, om, osd = row_statistics(T, COARSE[0], COARSE[1])
+        T = ((T - om[rows]) / osd[rows]).astype(np.float32)
+        out_mean, out_std = np.zeros(12, np.float32), np.ones(12, np.float32)
+        rowstats = (om, osd)
+    else:
+        out_mean, out_std = T.mean(0), T.std(0) + 1e-30
     mlp.set_normalization(in_mean, in_std, out_mean, out_std)
     dX = torch.from_numpy(X).cuda()
     dT = torch.from_numpy(T).cuda()
@@ -129,7 +150,11 @@ def train(X, T, epochs=8, batch=4096, lr=1e-3, seed=0, log=print):
             steps += 1
         history.append(float(np.mean(losses)))
         log(f"epoch {ep}: mean normalised MSE {history[-1]:.4f}")
-    return mlp, {"in_mean": in_mean, "in_std": in_std, "out_mean": out_mean, "out_std": out_std}, history
+    norm = {"in_mean": in_mean, "in_std": in_std, "out_mean": out_mean, "out_std": out_std}
+    if rowstats is not None:
+        mlp.set_row_normalization(*rowstats)
+        norm.update(row_mean=rowstats[0], row_std=rowstats[1])
+    return mlp, norm, history
 
 
 def rel_l2(x, y):
@@ -177,15 +202,16 @@ def main():
     ap.add_argument("--horizon-hours", type=float, default=12.0)
     ap.add_argument("--out", default="learned_result.json")
     ap.add_argument("--params-out", default="")
+    ap.add_argument("--row-norm", action="store_true", help="normalise the targets per latitude row")
     args = ap.parse_args()
     t0 = time.time()
     X, T = generate(args.pairs, args.train_seeds, stride=args.stride, target_steps=args.target_steps)
     t_gen = time.time() - t0
-    mlp, norm, hist = train(X, T, epochs=args.epochs)
+    mlp, norm, hist = train(X, T, epochs=args.epochs, row_norm=args.row_norm)
     t_train = time.time() - t0 - t_gen
     ev = evaluate(mlp, args.test_seed, args.horizon_hours * 3600.0)
     res = {"pairs": args.pairs, "samples": int(X.shape[0]), "train_seeds": args.train_seeds,
-           "target_steps": args.target_steps, "stride": args.stride,
+           "target_steps": args.target_steps, "stride": args.stride, "row_norm": args.row_norm,
            "test_seed": args.test_seed, "epochs": args.epochs, "loss_history": hist, "evaluation": ev,
            "seconds": {"generate": t_gen, "train": t_train, "evaluate": time.time() - t0 - t_gen - t_train}}
     with open(args.out, "w") as fh:

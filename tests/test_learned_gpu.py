@@ -137,6 +137,38 @@ def test_learned_source_matches_reference_and_keeps_mass():
         assert abs(s.total_mass() / m0 - 1) < 1e-8
 
 
+def test_row_normalised_source_matches_reference():
+    o, u = _coarse_state()
+    mlp = dgswe.MLP(60, 128, 12, seed=3)
+    X = learned.gather_inputs(u)
+    mlp.set_normalization(X.mean(0), X.std(0) + 1e-6, np.zeros(12, np.float32), np.ones(12, np.float32))
+    rng = np.random.default_rng(4)
+    om = (rng.normal(size=(36, 12)) * 1e-4).astype(np.float32)
+    osd = (1e-3 * (1 + rng.random((36, 12)))).astype(np.float32)
+    mlp.set_row_normalization(om, osd)
+    with dgswe.Solver(72, 36, 1, R, G, OMEGA, precision="fp32") as s:
+        k0 = s.rhs(u)
+        s.attach_mlp(mlp)
+        k1 = s.rhs(u)
+    p = mlp.get_params().astype(np.float64)
+    nrm = (X.mean(0).astype(np.float32).astype(np.float64), (X.std(0) + 1e-6).astype(np.float32).astype(np.float64),
+           np.zeros(12), np.ones(12))
+    y, _ = M.forward(p, X, nrm, 60, 128, 12)
+    rows = np.arange(36 * 72) // 72
+    src = (y * osd[rows] + om[rows]).reshape(36, 72, 3, 4)
+    c0 = np.array([[o.mass_matrix(j)[0, 0], o.mass_matrix(j)[0, 2]] for j in range(36)])
+    mass = (c0[:, None, 0] * src[..., 0, 0] + c0[:, None, 1] * src[..., 0, 2]).sum()
+    src[..., 0, 0] -= mass / (c0[:, 0].sum() * 72)
+    assert np.abs((k1 - k0) - src).max() < 1e-3 * np.abs(src).max()
+    # statistics of another mesh are refused when the source runs
+    mlp.set_row_normalization(om[:20], osd[:20])
+    with dgswe.Solver(72, 36, 1, R, G, OMEGA, precision="fp32") as s:
+        s.attach_mlp(mlp)
+        with pytest.raises(dgswe.DGError) as e:
+            s.rhs(u)
+        assert e.value.status == dgswe.DG_EINVAL
+
+
 def test_pipeline_end_to_end_reports_plain_vs_learned(capsys):
     """Reduced pipeline (64 pairs of one training run, 2 epochs, 1 h on a
     held-out seed): it runs on the library kernels end to end, the learned
