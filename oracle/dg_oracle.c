@@ -28,7 +28,7 @@
  *   Eq. (lin_adv) planar linear advection (validation problem)    -> flux_advection()
  *   Sec. 4.3 planar shallow water on the f-plane                  -> flux_plane_swe()
  *
- * Readings where the paper is silent (each one also listed in the design doc):
+ * Readings where the paper is silent:
  *   basis: orthonormal Legendre L_k = sqrt((2k+1)/2) P_k, mode m = b*n + a with
  *     a the lambda-degree; n = p+1 Gauss-Legendre points per direction for the
  *     volume, source and edge integrals; nm = p+9 points for mass matrices,
