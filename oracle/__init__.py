@@ -51,6 +51,8 @@ def lib():
         L.oracle_rhs_magnitude.argtypes = [ctypes.c_void_p, _dp, _dp]
         L.oracle_rhs_element.restype = ctypes.c_int
         L.oracle_rhs_element.argtypes = [ctypes.c_void_p, _dp, ctypes.c_int, ctypes.c_int, _dp]
+        L.oracle_rhs_magnitude_element.argtypes = [ctypes.c_void_p, _dp, ctypes.c_int, ctypes.c_int, _dp]
+        L.oracle_rhs_magnitude_element.restype = ctypes.c_int
         L.oracle_step.restype = ctypes.c_int
         L.oracle_step.argtypes = [ctypes.c_void_p, _dp, ctypes.c_int, ctypes.c_double, ctypes.c_int]
         L.oracle_rk_step.restype = ctypes.c_int
@@ -194,6 +196,15 @@ class Oracle:
         st = lib().oracle_rhs_element(self._h, _ptr(u), int(j), int(i), _ptr(out))
         if st:
             raise OracleError(f"rhs_element status {st}")
+        return out.reshape(self.nf, self.nphi)
+
+    def rhs_magnitude_element(self, u, j, i):
+        """The magnitude bound of one element's tendency."""
+        u = self._in(u)
+        out = np.empty(self.nf * self.nphi)
+        st = lib().oracle_rhs_magnitude_element(self._h, _ptr(u), int(j), int(i), _ptr(out))
+        if st:
+            raise OracleError(f"rhs_magnitude_element status {st}")
         return out.reshape(self.nf, self.nphi)
 
     def step(self, u, nsteps, dt, order=3):

@@ -277,3 +277,56 @@ def test_precision_switch_keeps_state():
         assert_within(state_err(s.get_state(), u), 1e-7, "to fp32")
         s.set_option(dgswe.OPT_PRECISION, dgswe.PREC["fp64"])
         assert_within(state_err(s.get_state(), u), 1e-7, "back to fp64")
+
+
+# --------------------------------------------- the largest mesh, sampled --
+
+def _large_state(nlon, nlat, p, seed):
+    """A seeded modal state for a mesh too large to project: element means of
+    the smooth field (mode 0) plus small seeded higher modes (any modal
+    coefficients are a valid DG state; the depth stays positive)."""
+    field = synth.SmoothField(seed)
+    lam = (np.arange(nlon) + 0.5) * (2 * math.pi / nlon)
+    th = -0.5 * math.pi + (np.arange(nlat) + 0.5) * (math.pi / nlat)
+    u = np.zeros((nlat, nlon, 3, (p + 1) ** 2))
+    rng = np.random.default_rng(seed)
+    for f, v in enumerate(field.fields_grid(lam, th)):
+        u[:, :, f, 0] = 2.0 * v
+        u[:, :, f, 1:] = rng.normal(size=(nlat, nlon, (p + 1) ** 2 - 1)) * (1e-3 * np.abs(v).max())
+    return u
+
+
+def test_rhs_parity_largest_mesh_sampled():
+    """1440 x 720, degree 4 (the largest bench mesh, 1.04 M elements): the
+    whole-mesh tendency of the FP64, FP32 and BF16 tensor-core stages against
+    the oracle's element-by-element tendency on sampled elements (pole rows,
+    the periodic seam, tile boundaries and random ones), each relative to the
+    element's own magnitude bound."""
+    nlon, nlat, p = 1440, 720, 4
+    u = _large_state(nlon, nlat, p, 3)
+    o = oracle_sphere(nlon, nlat, p)
+    rng = np.random.default_rng(0)
+    picks = {(0, 0), (0, nlon - 1), (nlat - 1, 0), (nlat - 1, nlon - 1), (nlat // 2, 0), (1, 719), (2, 720),
+             (3, 29), (4, 30), (7, 31), (8, 32), (nlat // 2 + 1, 47), (nlat - 2, 1)}
+    picks |= {(int(j), int(i)) for j, i in zip(rng.integers(0, nlat, 120), rng.integers(0, nlon, 120))}
+    want = {(j, i): (o.rhs_element(u, j, i), o.rhs_magnitude_element(u, j, i)) for j, i in sorted(picks)}
+    for prec, tol in (("fp64", 1e-12), ("fp32", 1e-5), ("fp32_tc_bf16", 8 * 2.0 ** -9)):
+        with solver(nlon, nlat, p, prec) as s:
+            k = s.rhs(u)
+        for (j, i), (kw, Sw) in want.items():
+            for f in range(3):
+                err = np.abs(k[j, i, f] - kw[f]).max() / Sw[f].max()
+                assert err <= tol, (prec, j, i, f, err)
+
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "fp32_tc_fp16"])
+def test_zero_steps_change_nothing(prec):
+    nlon, nlat, p = 12, 6, 2
+    _, u = case(nlon, nlat, p, 9)
+    with solver(nlon, nlat, p, prec) as s:
+        s.set_state(u)
+        before = s.get_state()
+        s.step(0, 1.0)
+        np.testing.assert_array_equal(s.get_state(), before)
+        assert s.stage_launches() == 0 and s.get_time() == 0.0
