@@ -84,7 +84,12 @@ typedef enum {
                                     default 16 */
     DG_OPT_TILE_ROWS = 7,        /* ensemble only: latitude rows per CTA tile, 4 or 8
                                     (default 8; dg_ensemble_autotune picks it) */
-    DG_OPT_BLOCKS_PER_SM = 8     /* ensemble only: persistent CTAs per SM, 1..8 (default 2) */
+    DG_OPT_BLOCKS_PER_SM = 8,    /* ensemble only: persistent CTAs per SM, 1..8 (default 2) */
+    DG_OPT_WELL_BALANCED = 9     /* 0 (default) / 1: remove from every tendency that of the
+                                    fluid at rest at the reference depth (the mean depth of the
+                                    state at dg_set_state), i.e. the quadrature residual of its
+                                    constant pressure, so that rest state is exactly steady;
+                                    FP64 then also stores h relative to that depth */
 } dg_option;
 
 /* Make CUDA device `device` current for the calling thread in this library

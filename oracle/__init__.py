@@ -40,6 +40,8 @@ def lib():
         L.oracle_destroy.argtypes = [ctypes.c_void_p]
         L.oracle_set_threads.argtypes = [ctypes.c_void_p, ctypes.c_int]
         L.oracle_set_alpha_mode.argtypes = [ctypes.c_void_p, ctypes.c_int]
+        L.oracle_set_well_balanced.argtypes = [ctypes.c_void_p, ctypes.c_double]
+        L.oracle_set_well_balanced.restype = ctypes.c_int
         L.oracle_set_alpha_mode.restype = ctypes.c_int
         L.oracle_state_len.restype = ctypes.c_size_t
         L.oracle_state_len.argtypes = [ctypes.c_void_p]
@@ -165,6 +167,12 @@ class Oracle:
         """0: local Rusanov alpha (default); 1: the global speeds of the stage input."""
         if lib().oracle_set_alpha_mode(self._h, int(mode)) != 0:
             raise ValueError(f"alpha mode {mode} not available for this oracle")
+
+    def set_well_balanced(self, href: float):
+        """href > 0: remove the tendency of the fluid at rest at depth href
+        from every tendency (that state becomes exactly steady); 0: off."""
+        if lib().oracle_set_well_balanced(self._h, float(href)) != 0:
+            raise ValueError("well-balanced option not available for this oracle")
 
     def _in(self, u):
         u = np.ascontiguousarray(u, dtype=np.float64).reshape(-1)

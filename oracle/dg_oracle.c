@@ -35,6 +35,9 @@
  *     projections and norms; local Rusanov alpha = max over both sides of the
  *     largest eigenvalue of dF/dU (resp. dG/dU); the whole numerical flux is zero
  *     on the pole edges; integrals in (lambda, theta) without R^2.
+ *   well-balanced option: the tendency of the fluid at rest at the
+ *     reference depth (the quadrature residual of its constant pressure) is
+ *     removed from every tendency, so that rest state is exactly steady.
  *   global Rusanov mode (optional): the one-sided speeds |u| + sqrt(gh) and
  *     |v| + sqrt(gh) of every face are replaced by their maxima over all Gauss
  *     points of the stage input, inside the same eigenvalue (so the lambda
@@ -68,6 +71,9 @@ typedef struct {
     double bx, by;     /* advection velocity (planar advection only) */
     int alpha_speed;   /* planar advection: 1 -> alpha = |beta|, 0 -> |beta . n| */
     int alpha_global;  /* sphere: 1 -> the wave speeds of every face are the global maxima */
+    /* well-balanced option (sphere): the tendency of the fluid at rest at
+     * depth href, per latitude row, is subtracted from every tendency */
+    double *rest_res, *rest_mag;   /* ny x nf*nphi, NULL when off */
     double x0, y0, dx, dy;
     double *xg, *wg;   /* n-point Gauss-Legendre rule on [-1, 1] */
     double *xm, *wm;   /* nm-point rule */
@@ -236,6 +242,7 @@ void oracle_destroy(oracle_ctx *c)
     if (!c) return;
     free(c->xg); free(c->wg); free(c->xm); free(c->wm); free(c->minv);
     free(c->phiv); free(c->dphix); free(c->dphiy); free(c->phie); free(c->phim);
+    free(c->rest_res); free(c->rest_mag);
     free(c);
 }
 
@@ -514,6 +521,35 @@ static int global_speeds(const oracle_ctx *c, const double *u, double *gs)
     return ORACLE_OK;
 }
 
+/* Well-balanced option on the sphere (href > 0; href <= 0 turns it off):
+ * every tendency has the tendency of the fluid at rest at depth href removed,
+ * so that state is exactly steady.  The rest state's tendency is the
+ * quadrature residual of its constant pressure (hv modes only); it is the
+ * same along a latitude row and is evaluated once per row. */
+int oracle_set_well_balanced(oracle_ctx *c, double href)
+{
+    free(c->rest_res); free(c->rest_mag);
+    c->rest_res = c->rest_mag = NULL;
+    if (!(href > 0.0)) return ORACLE_OK;
+    if (c->physics != PHYS_SPHERE_SWE) return ORACLE_EINVAL;
+    const size_t per = (size_t)c->nf * c->nphi;
+    double *rest = calloc((size_t)c->nx * c->ny * per, sizeof(double));
+    double *res = malloc(sizeof(double) * c->ny * per), *mag = malloc(sizeof(double) * c->ny * per);
+    if (!rest || !res || !mag) { free(rest); free(res); free(mag); return ORACLE_ENOMEM; }
+    /* h = href: mode 0 of the orthonormal basis is 1/2 everywhere */
+    for (size_t e = 0; e < (size_t)c->nx * c->ny; ++e) rest[e * per] = 2.0 * href;
+    int st = ORACLE_OK;
+    for (int jy = 0; jy < c->ny && st == ORACLE_OK; ++jy) {
+        st = rhs_element_impl(c, rest, jy, 0, res + jy * per, 0, NULL);
+        if (st == ORACLE_OK) st = rhs_element_impl(c, rest, jy, 0, mag + jy * per, 1, NULL);
+    }
+    free(rest);
+    if (st) { free(res); free(mag); return st; }
+    c->rest_res = res;
+    c->rest_mag = mag;
+    return ORACLE_OK;
+}
+
 /* Global Rusanov mode on the sphere: 1 -> every face uses the global speeds
  * of the stage input, 0 (default) -> the larger of the two one-sided ones. */
 int oracle_set_alpha_mode(oracle_ctx *c, int mode)
@@ -526,6 +562,17 @@ int oracle_set_alpha_mode(oracle_ctx *c, int mode)
 
 /* One element's tendency; in the global Rusanov mode the global speeds are
  * taken over the whole state u first (a full pass per call). */
+/* Well-balanced option: remove from a tendency (mag = 0) the tendency of the
+ * fluid at rest at the reference depth, or add its magnitude bound (mag = 1;
+ * the two evaluations round independently). */
+static void rest_correct(const oracle_ctx *c, int jy, double *out, int mag)
+{
+    if (!c->rest_res) return;
+    const size_t per = (size_t)c->nf * c->nphi;
+    for (size_t m = 0; m < per; ++m)
+        out[m] += mag ? c->rest_mag[jy * per + m] : -c->rest_res[jy * per + m];
+}
+
 int oracle_rhs_element(const oracle_ctx *c, const double *u, int jy, int ix, double *out)
 {
     double gs[2];
@@ -533,7 +580,9 @@ int oracle_rhs_element(const oracle_ctx *c, const double *u, int jy, int ix, dou
         int st = global_speeds(c, u, gs);
         if (st) return st;
     }
-    return rhs_element_impl(c, u, jy, ix, out, 0, c->alpha_global ? gs : NULL);
+    int st = rhs_element_impl(c, u, jy, ix, out, 0, c->alpha_global ? gs : NULL);
+    if (!st) rest_correct(c, jy, out, 0);
+    return st;
 }
 
 /* Magnitude bound of the tendency of element (jy, ix): the same assembly with
@@ -548,7 +597,9 @@ int oracle_rhs_magnitude_element(const oracle_ctx *c, const double *u, int jy, i
         int st = global_speeds(c, u, gs);
         if (st) return st;
     }
-    return rhs_element_impl(c, u, jy, ix, out, 1, c->alpha_global ? gs : NULL);
+    int st = rhs_element_impl(c, u, jy, ix, out, 1, c->alpha_global ? gs : NULL);
+    if (!st) rest_correct(c, jy, out, 1);
+    return st;
 }
 
 static int rhs_element_impl(const oracle_ctx *c, const double *u, int jy, int ix, double *out, int mag,
@@ -649,6 +700,7 @@ static int rhs_all(const oracle_ctx *c, const double *u, double *tend, int mag)
 #endif
     for (int e = 0; e < nel; ++e) {
         int st = rhs_element_impl(c, u, e / c->nx, e % c->nx, tend + (size_t)e * per, mag, gsp);
+        if (!st) rest_correct(c, e / c->nx, tend + (size_t)e * per, mag);
         if (st > status) status = st;
     }
     return status;

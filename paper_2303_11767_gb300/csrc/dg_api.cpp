@@ -95,7 +95,8 @@ struct dg_ctx {
     unsigned *d_status = nullptr;
     unsigned long long *d_maxbits = nullptr;
     void *galpha = nullptr;   // global Rusanov mode: the stage's two speeds (2 values of T)
-    double href = 0;      // reference depth of the resident state (FP32 path); 0 for FP64
+    double href = 0;      // reference depth of the resident state (FP32 path, or well balanced); else 0
+    int wb = 0;           // well-balanced option: the rest state at href is exactly steady
     double t = 0;
     bool have_state = false;
     long long launches = 0;       // fused stage kernels
@@ -166,7 +167,9 @@ StageArgs<T> base_args(dg_ctx *h, const RowTab<T> *rows, double href)
     a.nlon = h->nlon;
     a.nlat = h->nlat;
     a.href = (T)href;
-    a.P0 = (T)(0.5 * h->g * href * href);
+    // the pressure of the rest state at href enters through the per-row
+    // vector rho; the well-balanced option drops it (that state is steady)
+    a.P0 = h->wb ? T(0) : (T)(0.5 * h->g * href * href);
     a.g = (T)h->g;
     a.cF = (T)(2.0 / (h->R * h->tab.dlam));
     a.cG = (T)(2.0 / (h->R * h->tab.dth));
@@ -646,8 +649,11 @@ dg_status dg_set_option(dg_handle h, int key, long long value)
 {
     if (dg_status s = check(h)) return s;
     DeviceGuard dg(h->device);
-    if (h->physics != 0 && ((key == DG_OPT_PRECISION && value != DG_PREC_FP64) || (key == DG_OPT_ALPHA_MODE && value)))
-        return planar_unsupported(h, key == DG_OPT_PRECISION ? "a precision other than FP64" : "the global alpha mode");
+    if (h->physics != 0 && ((key == DG_OPT_PRECISION && value != DG_PREC_FP64) || (key == DG_OPT_ALPHA_MODE && value) ||
+                            (key == DG_OPT_WELL_BALANCED && value)))
+        return planar_unsupported(h, key == DG_OPT_PRECISION ? "a precision other than FP64"
+                                     : key == DG_OPT_ALPHA_MODE ? "the global alpha mode"
+                                                                : "the well-balanced option");
     switch (key) {
     case DG_OPT_PRECISION: {
         if (value < DG_PREC_FP64 || value > DG_PREC_FP32_TC_FP16) return fail(DG_EINVAL, "unknown precision %lld", value);
@@ -668,7 +674,7 @@ dg_status dg_set_option(dg_handle h, int key, long long value)
         if (dg_status s = alloc_state_buffers(h)) return s;
         h->cur = 0;
         if (h->have_state) {
-            if (h->f32()) {
+            if (h->f32() || h->wb) {
                 // reference depth: mean of the element mean depths
                 std::vector<double> m0(h->nel);
                 CUDA_TRY(cudaMemcpy2D(m0.data(), sizeof(double), h->stage64, sizeof(double) * 3 * h->nphi,
@@ -679,6 +685,32 @@ dg_status dg_set_option(dg_handle h, int key, long long value)
             } else {
                 h->href = 0.0;
             }
+            if (dg_status s = to_internal(h, h->stage64, h->B[0], h->L[0], h->href)) return s;
+            CUDA_TRY(cudaStreamSynchronize(h->stream));
+        }
+        return DG_OK;
+    }
+    case DG_OPT_WELL_BALANCED: {
+        if (value != 0 && value != 1) return fail(DG_EINVAL, "well-balanced option must be 0 or 1");
+        if (value == h->wb) return DG_OK;
+        CUDA_TRY(cudaStreamSynchronize(h->stream));
+        drop_graphs(h);
+        // the reference depth of the FP64 path changes: re-encode the state
+        if (h->have_state)
+            if (dg_status s = to_api(h, h->B[h->cur], h->L[h->cur], h->stage64, h->href)) return s;
+        h->wb = (int)value;
+        if (h->have_state) {
+            CUDA_TRY(cudaStreamSynchronize(h->stream));
+            h->href = 0.0;
+            if (h->f32() || h->wb) {
+                std::vector<double> m0(h->nel);
+                CUDA_TRY(cudaMemcpy2D(m0.data(), sizeof(double), h->stage64, sizeof(double) * 3 * h->nphi,
+                                      sizeof(double), h->nel, cudaMemcpyDeviceToHost));
+                double sum = 0;
+                for (double v : m0) sum += v;
+                h->href = 0.5 * sum / (double)h->nel;
+            }
+            h->cur = 0;
             if (dg_status s = to_internal(h, h->stage64, h->B[0], h->L[0], h->href)) return s;
             CUDA_TRY(cudaStreamSynchronize(h->stream));
         }
@@ -727,7 +759,7 @@ dg_status dg_set_state_device(dg_handle h, const double *d_modal, size_t len)
     }
     CUDA_TRY(cudaMemcpyAsync(h->stage64, d_modal, len * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
     h->href = 0.0;
-    if (h->f32()) {
+    if (h->f32() || h->wb) {
         std::vector<double> m0(h->nel);
         CUDA_TRY(cudaMemcpy2DAsync(m0.data(), sizeof(double), h->stage64, sizeof(double) * 3 * h->nphi,
                                    sizeof(double), h->nel, cudaMemcpyDeviceToHost, h->stream));
@@ -756,7 +788,7 @@ dg_status dg_set_state(dg_handle h, const double *modal, size_t len)
         return DG_OK;
     }
     CUDA_TRY(cudaMemcpyAsync(h->stage64, modal, len * sizeof(double), cudaMemcpyHostToDevice, h->stream));
-    h->href = h->f32() ? mean_depth(modal, h->nel, h->nphi) : 0.0;
+    h->href = (h->f32() || h->wb) ? mean_depth(modal, h->nel, h->nphi) : 0.0;
     h->cur = 0;
     if (dg_status s = to_internal(h, h->stage64, h->B[0], h->L[0], h->href)) return s;
     CUDA_TRY(cudaStreamSynchronize(h->stream));   // the host buffer is only borrowed
@@ -816,7 +848,7 @@ dg_status dg_rhs(dg_handle h, const double *modal_in, double *tend_out, size_t l
         if (h->check) return read_status(h);
         return DG_OK;
     }
-    const double href = h->f32() ? mean_depth(modal_in, h->nel, h->nphi) : 0.0;
+    const double href = (h->f32() || h->wb) ? mean_depth(modal_in, h->nel, h->nphi) : 0.0;
     CUDA_TRY(cudaMemcpyAsync(h->stage64, modal_in, len * sizeof(double), cudaMemcpyHostToDevice, h->stream));
     if (dg_status s = to_internal(h, h->stage64, in, nullptr, href)) return s;
     int r;
@@ -1167,7 +1199,7 @@ dg_status dg_restrict_from(dg_handle coarse, dg_handle fine)
                            coarse->rows64, tab, coarse->stream))
         return fail(DG_ECUDA, "restriction kernel failed: %s", cudaGetErrorString(cudaGetLastError()));
     coarse->href = 0.0;
-    if (coarse->f32()) {
+    if (coarse->f32() || coarse->wb) {
         std::vector<double> m0(coarse->nel);
         CUDA_TRY(cudaMemcpy2DAsync(m0.data(), sizeof(double), coarse->stage64, sizeof(double) * 3 * coarse->nphi,
                                    sizeof(double), coarse->nel, cudaMemcpyDeviceToHost, coarse->stream));

@@ -322,6 +322,43 @@ def test_plane_swe_rest_state_and_mass(p):
     assert abs(m1 / m0 - 1) < 1e-14
 
 
+# --------------------------------------------------------- well-balanced option --
+
+@pytest.mark.parametrize("p", [1, 2, 3])
+def test_well_balanced_option(p):
+    """The rest state at the reference depth is exactly steady; a rest state at
+    another depth H keeps the fraction (H^2 - href^2) / href^2 of the plain
+    residual (the residual is linear in the pressure g H^2 / 2); only hv
+    changes; mass is conserved."""
+    nlon, nlat, href = 16, 8, 5000.0
+    plain = sphere(nlon, nlat, p)
+    wb = sphere(nlon, nlat, p)
+    wb.set_well_balanced(href)
+
+    def rest(H):
+        u = np.zeros(plain.shape)
+        u[..., 0, 0] = 2.0 * H
+        return u
+
+    r0 = plain.rhs(rest(href))
+    assert np.abs(r0[..., 2, :]).max() > 0            # the plain scheme is not well balanced
+    assert np.abs(wb.rhs(rest(href))).max() <= 1e-14 * wb.rhs_magnitude(rest(href)).max()
+    H = 5200.0
+    want = (H * H - href * href) / (href * href) * r0
+    got = wb.rhs(rest(H))
+    S = wb.rhs_magnitude(rest(H)).max()
+    assert np.abs(got - want).max() <= 1e-13 * S
+    assert np.abs(got[..., 2, :] - want[..., 2, :]).max() <= 1e-7 * np.abs(want[..., 2, :]).max() + 1e-13 * S
+    u = wb.project_tensor(synth.SmoothField(4).fields_grid)
+    d = wb.rhs(u) - plain.rhs(u)
+    assert np.abs(d[..., 0, :]).max() == 0.0
+    assert np.abs(d[..., 1, :]).max() <= 1e-14 * plain.rhs_magnitude(u)[..., 1, :].max()
+    m0 = wb.total_mass(u)
+    assert abs(wb.total_mass(wb.step(u, 10, wb.max_dt(u, 0.1), 3)) / m0 - 1) < 1e-13
+    with pytest.raises(ValueError):
+        O.Oracle.plane_advection(4, 4, 1).set_well_balanced(1.0)
+
+
 # ----------------------------------------------------- conservation and rest --
 
 @pytest.mark.parametrize("nlon,nlat,p,nsteps", [(20, 10, 1, 100), (16, 8, 3, 40)])

@@ -330,3 +330,35 @@ def test_zero_steps_change_nothing(prec):
         s.step(0, 1.0)
         np.testing.assert_array_equal(s.get_state(), before)
         assert s.stage_launches() == 0 and s.get_time() == 0.0
+
+
+# --------------------------------------------------------- well-balanced option --
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32", 1e-5), ("fp32_tc_fp16", 8 * 2.0 ** -12)])
+def test_well_balanced_option_matches_oracle(prec, tol):
+    nlon, nlat, p = 44, 14, 3
+    u = case(nlon, nlat, p, 15)[1]
+    href = 0.5 * u[..., 0, 0].mean()          # the library's reference depth: the mean element depth
+    o = oracle_sphere(nlon, nlat, p)
+    o.set_well_balanced(href)
+    dt = o.max_dt(u, 0.1)
+    with solver(nlon, nlat, p, prec) as s:
+        s.set_state(u)
+        s.set_option(dgswe.OPT_WELL_BALANCED, 1)       # toggled with a resident state: kept
+        assert_within(state_err(s.get_state(), u), 1e-7 if prec != "fp64" else 1e-15, "state kept")
+        S = o.rhs_magnitude(u)
+        assert_within(tend_err(s.rhs(u), o.rhs(u), S), tol, f"well-balanced rhs {prec}")
+        rest = np.zeros_like(u)
+        rest[..., 0, 0] = 2.0 * 5000.0
+        assert np.abs(s.rhs(rest)).max() == 0.0       # the rest state is exactly steady
+        s.set_option(dgswe.OPT_STEPS_PER_GRAPH, 4)
+        s.set_state(u)
+        s.step(10, dt)
+        got = s.get_state()
+    want = o.step(u, 10, dt, 3)
+    if prec == "fp32_tc_fp16":
+        for f in range(3):
+            d = np.abs(got[..., f, :] - want[..., f, :]).max()
+            assert d <= 10 * dt * tol * S[..., f, :].max() + 1e-5 * np.abs(want[..., f, :]).max()
+    else:
+        assert_within(state_err(got, want), tol, f"well-balanced 10 steps {prec}")
