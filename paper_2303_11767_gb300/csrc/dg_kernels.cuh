@@ -74,6 +74,9 @@ struct Geo {
     static constexpr int TRC = bank_free_stride(12 * N, N, 32 / N);   // traces W,E,S,N x 3 x N
     static constexpr int EFC = bank_free_stride(6 * N, N, 32 / N);    // edge fluxes W,S x 3 x N
     static constexpr int HALO_MAX = 2 * W * N + 2 * G * N;
+    // the modes of the halo ring (at most 2 W + 2 G elements) staged in the
+    // edge-flux region, which is dead until the Rusanov phase
+    static constexpr bool HALO_STAGED = (2 * W + 2 * G) * EL <= TW * TH * EFC;
     static_assert(HALO_MAX <= 32 * W, "halo items exceed the block");
     static_assert(W * N + G * N <= 32 * W, "boundary flux items exceed the block");
 };
@@ -160,7 +163,11 @@ __device__ __forceinline__ void load_stage_row(const T *__restrict__ base, const
 }
 
 // One tile of G x W elements (tile column bx, tile row by) of one mesh.
-template <typename T, int N, int W>
+// STAGE_HALO: load the modes of the halo ring once into shared memory with
+// contiguous loads (pays when CTAs run in several waves, where the tile's
+// own latency overlaps other tiles); else each halo trace point reads its
+// element's rows from global memory (shorter critical path for one wave).
+template <typename T, int N, int W, bool STAGE_HALO = true>
 __device__ __forceinline__ void stage_tile(const StageArgs<T> &A, int bx, int by, unsigned char *smem_raw)
 {
     using GE = Geo<N, W>;
@@ -199,6 +206,33 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &A, int bx, int by
         else {
 #pragma unroll
             for (int a = 0; a < N; ++a) uh[f][a] = T(0);
+        }
+    }
+
+    // ---- S0 halo: the modes of the ring of neighbour elements facing the tile
+    //      (W / E columns, S / N rows; periodic in lambda, none across a pole),
+    //      loaded once by all threads with contiguous loads
+    const bool hasS = j0 > 0, hasN = j0 + Wv < A.nlat;
+    const int nSe = hasS ? Gv : 0, nNe = hasN ? Gv : 0;
+    if constexpr (STAGE_HALO && GE::HALO_STAGED) {
+        const int nH = 2 * Wv + nSe + nNe;
+        for (int v = tid; v < nH * EL; v += 32 * W) {
+            const int h = v / EL, c = v - h * EL;
+            int hj, hi;
+            if (h < 2 * Wv) {
+                const bool east = h >= Wv;
+                hj = j0 + (east ? h - Wv : h);
+                hi = east ? (i0 + Gv) % A.nlon : (i0 - 1 + A.nlon) % A.nlon;
+            } else {
+                const int r = h - 2 * Wv;
+                const bool north = r >= nSe;
+                hj = north ? j0 + Wv : j0 - 1;
+                hi = i0 + (north ? r - nSe : r);
+            }
+            const size_t o = ((size_t)hj * A.nlon + hi) * EL + c;
+            T val = __ldg(A.base + o);
+            if (A.inc) val += __ldg(A.inc + o);
+            ef[v] = val;
         }
     }
 
@@ -280,13 +314,13 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &A, int bx, int by
     }
 
     // ---- S4 halo: traces of the ring of neighbour elements facing the tile
+    if constexpr (STAGE_HALO && GE::HALO_STAGED) __syncthreads();   // the ring's modes are in shared memory
     {
         const int nWE = Wv * N;
-        const bool hasS = j0 > 0, hasN = j0 + Wv < A.nlat;
         const int nS = hasS ? Gv * N : 0, nN = hasN ? Gv * N : 0;
         const int it = tid;   // whole warps take halo items (no divergence inside a warp)
         if (it < 2 * nWE + nS + nN) {
-            int he_i, he_j, side, kk, sl;
+            int he_i, he_j, side, kk, sl, hh;
             if (it < 2 * nWE) {                 // west / east halo columns
                 const bool east = it >= nWE;
                 const int r = east ? it - nWE : it;
@@ -296,6 +330,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &A, int bx, int by
                 he_i = east ? (i0 + Gv) % A.nlon : (i0 - 1 + A.nlon) % A.nlon;
                 side = east ? 0 : 1;            // east halo needs its W trace
                 sl = (w + 1) * TW + (east ? Gv + 1 : 0);
+                hh = east ? Wv + w : w;
             } else {                            // south / north halo rows
                 const int r0 = it - 2 * nWE;
                 const bool north = r0 >= nS;
@@ -306,8 +341,18 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &A, int bx, int by
                 he_j = north ? j0 + Wv : j0 - 1;
                 side = north ? 2 : 3;           // north halo needs its S trace
                 sl = (north ? Wv + 1 : 0) * TW + c + 1;
+                hh = 2 * Wv + (north ? nSe + c : c);
             }
             const size_t hoff = ((size_t)he_j * A.nlon + he_i) * EL;
+            // row b of field f of the halo element: staged, or from global memory
+            auto halo_row = [&](int f, int b, T *row) {
+                if constexpr (STAGE_HALO && GE::HALO_STAGED) {
+#pragma unroll
+                    for (int a = 0; a < N; ++a) row[a] = ef[hh * EL + f * NP + b * N + a];
+                } else {
+                    load_stage_row<T, N>(A.base, A.inc, hoff + f * NP + b * N, row);
+                }
+            };
             T *slot = trc + sl * TRC;
 #pragma unroll
             for (int f = 0; f < 3; ++f) {
@@ -316,7 +361,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &A, int bx, int by
 #pragma unroll
                     for (int b = 0; b < N; ++b) {
                         T row[N];
-                        load_stage_row<T, N>(A.base, A.inc, hoff + f * NP + b * N, row);
+                        halo_row(f, b, row);
                         T s = T(0);
 #pragma unroll
                         for (int a = 0; a < N; ++a) s = fma(side == 1 ? B.SE[a] : B.SW[a], row[a], s);
@@ -326,7 +371,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &A, int bx, int by
 #pragma unroll
                     for (int b = 0; b < N; ++b) {
                         T row[N];
-                        load_stage_row<T, N>(A.base, A.inc, hoff + f * NP + b * N, row);
+                        halo_row(f, b, row);
                         T s = T(0);
 #pragma unroll
                         for (int a = 0; a < N; ++a) s = fma(B.LV[a][kk], row[a], s);
@@ -552,12 +597,12 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &A, int bx, int by
     if (st && valid) atomicOr(A.status, st);
 }
 
-template <typename T, int N, int W>
+template <typename T, int N, int W, bool STAGE_HALO>
 __global__ void __launch_bounds__(32 * W) stage_kernel(const StageArgs<T> A)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     pdl_wait();
-    stage_tile<T, N, W>(A, blockIdx.x, blockIdx.y, smem_raw);
+    stage_tile<T, N, W, STAGE_HALO>(A, blockIdx.x, blockIdx.y, smem_raw);
     pdl_launch_dependents();
 }
 
@@ -574,18 +619,31 @@ int launch_stage_n(const StageArgs<T> &a, cudaStream_t s)
     constexpr int W = DG_WARPS;
     using GE = Geo<N, W>;
     const size_t smem = stage_smem_bytes<T, N, W>();
-    // the shared-memory opt-in is a per-device function attribute
+    // the shared-memory opt-in is a per-device function attribute; one wave
+    // of the kernel holds SMs x (resident CTAs per SM) tiles
     static unsigned long long attr_set = 0;
+    static int wave[64];
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 1;
     if (!(attr_set >> dev & 1ull)) {
-        if (cudaFuncSetAttribute(stage_kernel<T, N, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-            cudaSuccess)
+        int sms = 0, per = 0;
+        if (cudaFuncSetAttribute(stage_kernel<T, N, W, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem) != cudaSuccess ||
+            cudaFuncSetAttribute(stage_kernel<T, N, W, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, stage_kernel<T, N, W, true>, 32 * W, smem) !=
+                cudaSuccess)
             return 1;
+        wave[dev] = sms * (per > 0 ? per : 1);
         attr_set |= 1ull << dev;
     }
     dim3 grid((a.nlon + GE::G - 1) / GE::G, (a.nlat + W - 1) / W);
-    if (launch_pdl(stage_kernel<T, N, W>, grid, dim3(32 * W), smem, s, a) != cudaSuccess) return 1;
+    // stage the halo ring only when the tiles run in more than one wave
+    const bool staged = (long long)grid.x * grid.y > wave[dev];
+    const cudaError_t e = staged ? launch_pdl(stage_kernel<T, N, W, true>, grid, dim3(32 * W), smem, s, a)
+                                 : launch_pdl(stage_kernel<T, N, W, false>, grid, dim3(32 * W), smem, s, a);
+    if (e != cudaSuccess) return 1;
     return cudaPeekAtLastError() == cudaSuccess ? 0 : 1;
 }
 
