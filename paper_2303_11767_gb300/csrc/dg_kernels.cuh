@@ -74,12 +74,47 @@ struct Geo {
     static constexpr int TRC = bank_free_stride(12 * N, N, 32 / N);   // traces W,E,S,N x 3 x N
     static constexpr int EFC = bank_free_stride(6 * N, N, 32 / N);    // edge fluxes W,S x 3 x N
     static constexpr int HALO_MAX = 2 * W * N + 2 * G * N;
-    // the modes of the halo ring (at most 2 W + 2 G elements) staged in the
-    // edge-flux region, which is dead until the Rusanov phase
-    static constexpr bool HALO_STAGED = (2 * W + 2 * G) * EL <= TW * TH * EFC;
+    // values of one copy of the halo ring's modes (at most 2 W + 2 G elements)
+    static constexpr int HALO_CAP = (2 * W + 2 * G) * EL;
     static_assert(HALO_MAX <= 32 * W, "halo items exceed the block");
     static_assert(W * N + G * N <= 32 * W, "boundary flux items exceed the block");
 };
+
+// Shared-memory map of one tile, in elements of T: the warp buffers, the
+// trace slots, then the edge-flux region.  The edge-flux region is dead until
+// the Rusanov phase, so the halo ring's modes (stage base, then increment)
+// are staged there first; it starts on a 16-byte boundary for the
+// asynchronous copies and is as long as the larger of the two uses.
+template <typename T, int N, int W>
+struct SmemMap {
+    using GE = Geo<N, W>;
+    static constexpr int VA = 16 / (int)sizeof(T);
+    static constexpr int TRC_OFF = W * GE::G * GE::WB;
+    static constexpr int EF_OFF = (TRC_OFF + GE::TW * GE::TH * GE::TRC + VA - 1) / VA * VA;
+    static constexpr int EF_LEN = GE::TW * GE::TH * GE::EFC > 2 * GE::HALO_CAP ? GE::TW * GE::TH * GE::EFC
+                                                                             : 2 * GE::HALO_CAP;
+    static constexpr size_t BYTES = sizeof(T) * (size_t)(EF_OFF + EF_LEN);
+    // bytes per asynchronous copy: the largest of 16 / 8 / 4 that divides an
+    // element's modes (elements are contiguous and the arrays 16-byte aligned)
+    static constexpr int CP = (GE::EL * (int)sizeof(T)) % 16 == 0 ? 16
+                              : (GE::EL * (int)sizeof(T)) % 8 == 0 ? 8
+                                                                   : 4;
+};
+
+// Asynchronous global -> shared copy of CP bytes (both addresses CP-aligned);
+// it completes at cp_async_wait_all, and a block barrier then publishes it.
+template <int CP>
+__device__ __forceinline__ void cp_async(void *dst, const void *src)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    const size_t g = __cvta_generic_to_global(src);
+    if constexpr (CP == 16)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(g) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(d), "l"(g), "n"(CP) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 template <typename T, int N>
 __device__ __forceinline__ void load_row(const T *__restrict__ p, T *o)
@@ -162,12 +197,11 @@ __device__ __forceinline__ void load_stage_row(const T *__restrict__ base, const
     }
 }
 
-// One tile of G x W elements (tile column bx, tile row by) of one mesh.
-// STAGE_HALO: load the modes of the halo ring once into shared memory with
-// contiguous loads (pays when CTAs run in several waves, where the tile's
-// own latency overlaps other tiles); else each halo trace point reads its
-// element's rows from global memory (shorter critical path for one wave).
-template <typename T, int N, int W, bool STAGE_HALO = true>
+// One tile of G x W elements (tile column bx, tile row by) of one mesh.  The
+// modes of the tile's halo ring reach shared memory through asynchronous
+// contiguous copies issued at the start of the tile, so that their latency
+// overlaps the tile's own S1 / S4 work.
+template <typename T, int N, int W>
 __device__ __forceinline__ void stage_tile(const StageArgs<T> &A, int bx, int by, unsigned char *smem_raw)
 {
     using GE = Geo<N, W>;
@@ -175,9 +209,10 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &A, int bx, int by
     constexpr int TW = GE::TW, TRC = GE::TRC, EFC = GE::EFC;
     const BasisTab<T> &B = c_basis[N - 1];
 
+    using SM = SmemMap<T, N, W>;
     T *wbuf = reinterpret_cast<T *>(smem_raw);
-    T *trc = wbuf + W * G * WB;              // [slot][W,E,S,N][f][N] traces
-    T *ef = trc + TW * GE::TH * TRC;         // [slot][W,S][f][N] edge fluxes
+    T *trc = wbuf + SM::TRC_OFF;             // [slot][W,E,S,N][f][N] traces
+    T *ef = wbuf + SM::EF_OFF;               // [slot][W,S][f][N] edge fluxes
 
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
@@ -211,13 +246,15 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &A, int bx, int by
 
     // ---- S0 halo: the modes of the ring of neighbour elements facing the tile
     //      (W / E columns, S / N rows; periodic in lambda, none across a pole),
-    //      loaded once by all threads with contiguous loads
+    //      copied asynchronously by all threads, the base to ef[0, HALO_CAP)
+    //      and the increment to ef[HALO_CAP, 2 HALO_CAP)
     const bool hasS = j0 > 0, hasN = j0 + Wv < A.nlat;
     const int nSe = hasS ? Gv : 0, nNe = hasN ? Gv : 0;
-    if constexpr (STAGE_HALO && GE::HALO_STAGED) {
+    {
+        constexpr int VPC = SM::CP / (int)sizeof(T), CPE = EL / VPC;
         const int nH = 2 * Wv + nSe + nNe;
-        for (int v = tid; v < nH * EL; v += 32 * W) {
-            const int h = v / EL, c = v - h * EL;
+        for (int v = tid; v < nH * CPE; v += 32 * W) {
+            const int h = v / CPE, c = (v - h * CPE) * VPC;
             int hj, hi;
             if (h < 2 * Wv) {
                 const bool east = h >= Wv;
@@ -230,9 +267,8 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &A, int bx, int by
                 hi = i0 + (north ? r - nSe : r);
             }
             const size_t o = ((size_t)hj * A.nlon + hi) * EL + c;
-            T val = __ldg(A.base + o);
-            if (A.inc) val += __ldg(A.inc + o);
-            ef[v] = val;
+            cp_async<SM::CP>(ef + h * EL + c, A.base + o);
+            if (A.inc) cp_async<SM::CP>(ef + GE::HALO_CAP + h * EL + c, A.inc + o);
         }
     }
 
@@ -314,20 +350,19 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &A, int bx, int by
     }
 
     // ---- S4 halo: traces of the ring of neighbour elements facing the tile
-    if constexpr (STAGE_HALO && GE::HALO_STAGED) __syncthreads();   // the ring's modes are in shared memory
+    cp_async_wait_all();   // the ring's modes are in shared memory
+    __syncthreads();
     {
         const int nWE = Wv * N;
         const int nS = hasS ? Gv * N : 0, nN = hasN ? Gv * N : 0;
         const int it = tid;   // whole warps take halo items (no divergence inside a warp)
         if (it < 2 * nWE + nS + nN) {
-            int he_i, he_j, side, kk, sl, hh;
+            int side, kk, sl, hh;
             if (it < 2 * nWE) {                 // west / east halo columns
                 const bool east = it >= nWE;
                 const int r = east ? it - nWE : it;
                 const int w = r / N;
                 kk = r - w * N;
-                he_j = j0 + w;
-                he_i = east ? (i0 + Gv) % A.nlon : (i0 - 1 + A.nlon) % A.nlon;
                 side = east ? 0 : 1;            // east halo needs its W trace
                 sl = (w + 1) * TW + (east ? Gv + 1 : 0);
                 hh = east ? Wv + w : w;
@@ -337,20 +372,18 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &A, int bx, int by
                 const int r = north ? r0 - nS : r0;
                 const int c = r / N;
                 kk = r - c * N;
-                he_i = i0 + c;
-                he_j = north ? j0 + Wv : j0 - 1;
                 side = north ? 2 : 3;           // north halo needs its S trace
                 sl = (north ? Wv + 1 : 0) * TW + c + 1;
                 hh = 2 * Wv + (north ? nSe + c : c);
             }
-            const size_t hoff = ((size_t)he_j * A.nlon + he_i) * EL;
-            // row b of field f of the halo element: staged, or from global memory
+            // row b of field f of the halo element's stage state
             auto halo_row = [&](int f, int b, T *row) {
-                if constexpr (STAGE_HALO && GE::HALO_STAGED) {
+                const T *hb = ef + hh * EL + f * NP + b * N;
 #pragma unroll
-                    for (int a = 0; a < N; ++a) row[a] = ef[hh * EL + f * NP + b * N + a];
-                } else {
-                    load_stage_row<T, N>(A.base, A.inc, hoff + f * NP + b * N, row);
+                for (int a = 0; a < N; ++a) row[a] = hb[a];
+                if (A.inc) {
+#pragma unroll
+                    for (int a = 0; a < N; ++a) row[a] += hb[GE::HALO_CAP + a];
                 }
             };
             T *slot = trc + sl * TRC;
@@ -597,20 +630,19 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &A, int bx, int by
     if (st && valid) atomicOr(A.status, st);
 }
 
-template <typename T, int N, int W, bool STAGE_HALO>
+template <typename T, int N, int W>
 __global__ void __launch_bounds__(32 * W) stage_kernel(const StageArgs<T> A)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     pdl_wait();
-    stage_tile<T, N, W, STAGE_HALO>(A, blockIdx.x, blockIdx.y, smem_raw);
+    stage_tile<T, N, W>(A, blockIdx.x, blockIdx.y, smem_raw);
     pdl_launch_dependents();
 }
 
 template <typename T, int N, int W>
 constexpr size_t stage_smem_bytes()
 {
-    using GE = Geo<N, W>;
-    return sizeof(T) * ((size_t)W * GE::G * GE::WB + (size_t)GE::TW * GE::TH * (GE::TRC + GE::EFC));
+    return SmemMap<T, N, W>::BYTES;
 }
 
 template <typename T, int N>
@@ -619,31 +651,18 @@ int launch_stage_n(const StageArgs<T> &a, cudaStream_t s)
     constexpr int W = DG_WARPS;
     using GE = Geo<N, W>;
     const size_t smem = stage_smem_bytes<T, N, W>();
-    // the shared-memory opt-in is a per-device function attribute; one wave
-    // of the kernel holds SMs x (resident CTAs per SM) tiles
+    // the shared-memory opt-in is a per-device function attribute
     static unsigned long long attr_set = 0;
-    static int wave[64];
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 1;
     if (!(attr_set >> dev & 1ull)) {
-        int sms = 0, per = 0;
-        if (cudaFuncSetAttribute(stage_kernel<T, N, W, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem) != cudaSuccess ||
-            cudaFuncSetAttribute(stage_kernel<T, N, W, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem) != cudaSuccess ||
-            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, stage_kernel<T, N, W, true>, 32 * W, smem) !=
-                cudaSuccess)
+        if (cudaFuncSetAttribute(stage_kernel<T, N, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+            cudaSuccess)
             return 1;
-        wave[dev] = sms * (per > 0 ? per : 1);
         attr_set |= 1ull << dev;
     }
     dim3 grid((a.nlon + GE::G - 1) / GE::G, (a.nlat + W - 1) / W);
-    // stage the halo ring only when the tiles run in more than one wave
-    const bool staged = (long long)grid.x * grid.y > wave[dev];
-    const cudaError_t e = staged ? launch_pdl(stage_kernel<T, N, W, true>, grid, dim3(32 * W), smem, s, a)
-                                 : launch_pdl(stage_kernel<T, N, W, false>, grid, dim3(32 * W), smem, s, a);
-    if (e != cudaSuccess) return 1;
+    if (launch_pdl(stage_kernel<T, N, W>, grid, dim3(32 * W), smem, s, a) != cudaSuccess) return 1;
     return cudaPeekAtLastError() == cudaSuccess ? 0 : 1;
 }
 
