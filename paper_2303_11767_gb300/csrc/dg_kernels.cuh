@@ -25,6 +25,7 @@
 
 #include <cuda_runtime.h>
 #include <cstdint>
+#include <type_traits>
 
 #include "dg_internal.h"
 #include "dg_flux.cuh"
@@ -115,6 +116,50 @@ __device__ __forceinline__ void cp_async(void *dst, const void *src)
 }
 
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// The FP32 stage at p <= 3 runs its contractions and its Runge-Kutta update
+// on the paired FP32 instructions of sm_100+ (two independent FMAs or adds
+// per instruction, each rounded exactly as the scalar one, so the results are
+// unchanged); at p = 4 the pairs' extra registers would cost a resident CTA
+// per SM and the scalar form is kept.
+template <typename T, int N>
+__host__ __device__ constexpr bool use_f2()
+{
+    return std::is_same<T, float>::value && N <= 4;
+}
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ float2 bc2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+// number of leading entries of an N-vector handled in pairs
+template <typename T, int N>
+__host__ __device__ constexpr int pair_len()
+{
+    return use_f2<T, N>() ? N - (N & 1) : 0;
+}
+
+// y[q] = sum_a M[a][q] x[a] for q < N, accumulated in a = 0..N-1 order
+template <typename T, int N>
+__device__ __forceinline__ void colsum(const T (&M)[DG_MAXN][DG_MAXN], const T *x, T *y)
+{
+    constexpr int PL = pair_len<T, N>();
+    if constexpr (PL > 0) {
+#pragma unroll
+        for (int q = 0; q < PL; q += 2) {
+            float2 s = bc2(0.f);
+#pragma unroll
+            for (int a = 0; a < N; ++a) s = __ffma2_rn(f2(M[a][q], M[a][q + 1]), bc2(x[a]), s);
+            y[q] = s.x;
+            y[q + 1] = s.y;
+        }
+    }
+#pragma unroll
+    for (int q = PL; q < N; ++q) {
+        T s = T(0);
+#pragma unroll
+        for (int a = 0; a < N; ++a) s = fma(M[a][q], x[a], s);
+        y[q] = s;
+    }
+}
 
 template <typename T, int N>
 __device__ __forceinline__ void load_row(const T *__restrict__ p, T *o)
@@ -288,13 +333,10 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &A, int bx, int by
     if (lane_ok) {
 #pragma unroll
         for (int f = 0; f < 3; ++f) {
+            T t1[N];
+            colsum<T, N>(B.LV, uh[f], t1);
 #pragma unroll
-            for (int q = 0; q < N; ++q) {
-                T s = T(0);
-#pragma unroll
-                for (int a = 0; a < N; ++a) s = fma(B.LV[a][q], uh[f][a], s);
-                wb[GE::T1_OFF + (f * N + q) * SA + k] = s;
-            }
+            for (int q = 0; q < N; ++q) wb[GE::T1_OFF + (f * N + q) * SA + k] = t1[q];
             T se = T(0), sw = T(0);
 #pragma unroll
             for (int a = 0; a < N; ++a) {
@@ -323,13 +365,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &A, int bx, int by
                 ee[b] = wb[GE::EW_OFF + (f * 2 + 0) * N + b];
                 ew[b] = wb[GE::EW_OFF + (f * 2 + 1) * N + b];
             }
-#pragma unroll
-            for (int q = 0; q < N; ++q) {
-                T s = T(0);
-#pragma unroll
-                for (int b = 0; b < N; ++b) s = fma(B.LV[b][q], c[b], s);
-                qn[f][q] = s;
-            }
+            colsum<T, N>(B.LV, c, qn[f]);
             T ts = T(0), tn = T(0), tw = T(0), te = T(0);
 #pragma unroll
             for (int b = 0; b < N; ++b) {
@@ -504,8 +540,29 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &A, int bx, int by
             const T G0 = cGc * hv, G1 = cGc * (hv * u), G2 = cGc * fma(hv, v, P);
             const T K = s * fma(A.twoOmega, c, u * A.invR);
             const T S1 = K * hv, S2 = -(P * s * A.invR) - K * hu;
+            constexpr int PL = pair_len<T, N>();
+            if constexpr (PL > 0) {
 #pragma unroll
-            for (int b = 0; b < N; ++b) {
+                for (int b = 0; b < PL; b += 2) {
+                    const float2 wl = f2(__ldg(&RT->QT[q][b]), __ldg(&RT->QT[q][b + 1]));
+                    const float2 wd = f2(__ldg(&RT->PT[q][b]), __ldg(&RT->PT[q][b + 1]));
+                    float2 x;
+                    x = __ffma2_rn(wl, bc2(F0), f2(X1[0][b], X1[0][b + 1]));
+                    X1[0][b] = x.x, X1[0][b + 1] = x.y;
+                    x = __ffma2_rn(wl, bc2(F1), f2(X1[1][b], X1[1][b + 1]));
+                    X1[1][b] = x.x, X1[1][b + 1] = x.y;
+                    x = __ffma2_rn(wl, bc2(F2), f2(X1[2][b], X1[2][b + 1]));
+                    X1[2][b] = x.x, X1[2][b + 1] = x.y;
+                    x = __ffma2_rn(wd, bc2(G0), f2(X2[0][b], X2[0][b + 1]));
+                    X2[0][b] = x.x, X2[0][b + 1] = x.y;
+                    x = __ffma2_rn(wd, bc2(G1), __ffma2_rn(wl, bc2(S1), f2(X2[1][b], X2[1][b + 1])));
+                    X2[1][b] = x.x, X2[1][b + 1] = x.y;
+                    x = __ffma2_rn(wd, bc2(G2), __ffma2_rn(wl, bc2(S2), f2(X2[2][b], X2[2][b + 1])));
+                    X2[2][b] = x.x, X2[2][b + 1] = x.y;
+                }
+            }
+#pragma unroll
+            for (int b = PL; b < N; ++b) {
                 const T wl = __ldg(&RT->QT[q][b]), wd = __ldg(&RT->PT[q][b]);
                 X1[0][b] = fma(wl, F0, X1[0][b]);
                 X1[1][b] = fma(wl, F1, X1[1][b]);
@@ -547,8 +604,21 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &A, int bx, int by
                 ye = fma(Qk[q], efE[f * N + q], ye);
                 yw = fma(Qk[q], efW[f * N + q], yw);
             }
+            constexpr int PL = pair_len<T, N>();
+            if constexpr (PL > 0) {
 #pragma unroll
-            for (int a = 0; a < N; ++a) {
+                for (int a = 0; a < PL; a += 2) {
+                    float2 s = bc2(0.f);
+#pragma unroll
+                    for (int q = 0; q < N; ++q)
+                        s = __ffma2_rn(f2(B.WLD[a][q], B.WLD[a + 1][q]), bc2(y1[q]),
+                                       __ffma2_rn(f2(B.WLV[a][q], B.WLV[a + 1][q]), bc2(y2[q]), s));
+                    kk[f][a] = s.x - (B.SE[a] * ye - B.SW[a] * yw);
+                    kk[f][a + 1] = s.y - (B.SE[a + 1] * ye - B.SW[a + 1] * yw);
+                }
+            }
+#pragma unroll
+            for (int a = PL; a < N; ++a) {
                 T s = T(0);
 #pragma unroll
                 for (int q = 0; q < N; ++q) s = fma(B.WLD[a][q], y1[q], fma(B.WLV[a][q], y2[q], s));
@@ -609,8 +679,28 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &A, int bx, int by
 #pragma unroll
                         for (int a = 0; a < N; ++a) lo[a] = T(0);
                     }
+                    constexpr int PL = pair_len<T, N>();
+                    if constexpr (PL > 0) {
 #pragma unroll
-                    for (int a = 0; a < N; ++a) {
+                        for (int a = 0; a < PL; a += 2) {
+                            const float2 bs2 = f2(bs[a], bs[a + 1]);
+                            const float2 delta = __ffma2_rn(bc2(cdt), f2(kk[f][a], kk[f][a + 1]),
+                                                            __ffma2_rn(bc2(A.cd), f2(acc[a], acc[a + 1]),
+                                                                       __fmul2_rn(bc2(A.ci), f2(inc[a], inc[a + 1]))));
+                            const float2 s1 = __fadd2_rn(bs2, delta);
+                            const float2 bp = __fadd2_rn(s1, neg2(bs2));
+                            const float2 err = __fadd2_rn(__fadd2_rn(bs2, neg2(__fadd2_rn(s1, neg2(bp)))),
+                                                          __fadd2_rn(delta, neg2(bp)));
+                            const float2 l1 = __fadd2_rn(f2(lo[a], lo[a + 1]), err);
+                            const float2 hi = __fadd2_rn(s1, l1);
+                            const float2 ol2 = __fadd2_rn(l1, neg2(__fadd2_rn(hi, neg2(s1))));
+                            ob[a] = hi.x, ob[a + 1] = hi.y;
+                            ol[a] = ol2.x, ol[a + 1] = ol2.y;
+                            if (!isfinite(hi.x) || !isfinite(hi.y)) st |= DG_STATUS_NONFINITE;
+                        }
+                    }
+#pragma unroll
+                    for (int a = PL; a < N; ++a) {
                         const T delta = fma(cdt, kk[f][a], fma(A.cd, acc[a], A.ci * inc[a]));
                         const T s1 = bs[a] + delta;
                         const T bp = s1 - bs[a];
