@@ -251,7 +251,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &A, int bx, int by
 {
     using GE = Geo<N, W>;
     constexpr int G = GE::G, NP = GE::NP, EL = GE::EL, SA = GE::SA, WB = GE::WB;
-    constexpr int TW = GE::TW, TRC = GE::TRC, EFC = GE::EFC;
+    constexpr int TW = GE::TW, TRC = GE::TRC;
     const BasisTab<T> &B = c_basis[N - 1];
 
     using SM = SmemMap<T, N, W>;
