@@ -298,13 +298,19 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &A, int bx, int by
     {
         constexpr int VPC = SM::CP / (int)sizeof(T), CPE = EL / VPC;
         const int nH = 2 * Wv + nSe + nNe;
+        // The periodic W / E columns are found in the loop for 16-byte pieces
+        // (one or two per thread) and once before it for the 4- and 8-byte
+        // pieces (several per thread): the faster form measured for each.
+        constexpr bool WRAP_ONCE = SM::CP < 16;
+        const int iW = i0 > 0 ? i0 - 1 : A.nlon - 1, iE = i0 + Gv < A.nlon ? i0 + Gv : 0;   // i0 + Gv <= nlon
         for (int v = tid; v < nH * CPE; v += 32 * W) {
             const int h = v / CPE, c = (v - h * CPE) * VPC;
             int hj, hi;
             if (h < 2 * Wv) {
                 const bool east = h >= Wv;
                 hj = j0 + (east ? h - Wv : h);
-                hi = east ? (i0 + Gv) % A.nlon : (i0 - 1 + A.nlon) % A.nlon;
+                if constexpr (WRAP_ONCE) hi = east ? iE : iW;
+                else hi = east ? (i0 + Gv) % A.nlon : (i0 - 1 + A.nlon) % A.nlon;
             } else {
                 const int r = h - 2 * Wv;
                 const bool north = r >= nSe;

@@ -285,7 +285,10 @@ __global__ void __launch_bounds__(128 * TC_TPE, 2) tc_stage_kernel(const StageAr
     const int j = row_ok ? j0 + q4 : j0;   // rows past the mesh borrow the first row's tables
     const bool lane_ok = l <= Gv + 1;
     const bool interior = row_ok && l >= 1 && l <= Gv;
-    const int i = ((i0 + l - 1) % A.nlon + A.nlon) % A.nlon;
+    // longitude of lane l (lanes 0 and Gv + 1 are the W / E halo columns,
+    // periodic in lambda; lanes past Gv + 1 load nothing)
+    const int il = i0 + l - 1;
+    const int i = !lane_ok ? 0 : il < 0 ? il + A.nlon : il >= A.nlon ? il - A.nlon : il;
     const size_t rowlen = (size_t)3 * NP * A.nlon;
     const float href = A.href, gg = A.g;
     unsigned st = 0, st_int = 0;   // status of any thread / of interior elements only
