@@ -51,7 +51,7 @@ typedef enum {
     DG_ENONFINITE = 4,      /* a NaN or Inf appeared in the state or tendency */
     DG_ENONPHYSICAL = 5,    /* h <= 0 at a quadrature point (u = hu/h undefined) */
     DG_ETIMEOUT = 6,        /* a bounded device-side wait gave up */
-    DG_EUNSUPPORTED = 7     /* valid request that this build does not implement */
+    DG_EUNSUPPORTED = 7     /* valid request that the library does not implement */
 } dg_status;
 
 typedef enum {

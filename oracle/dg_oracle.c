@@ -3,10 +3,11 @@
  * Galerkin discretisation of the rotating shallow water equations on a
  * longitude-latitude mesh of the sphere (arxiv 2303.11767, Sec. 2).
  *
- * TEST INFRASTRUCTURE ONLY.  This file is the judge of parity for the CUDA
- * path.  Only the test suite, the smoke check and the CPU-baseline leg of the
- * benchmark may load it.  It shares no code, header, table or constant
- * generator with the CUDA library, and the CUDA library never calls it.
+ * TEST INFRASTRUCTURE ONLY.  This file is the reference that the CUDA path
+ * is checked against.  Only the test suite, the smoke check and the
+ * CPU-baseline leg of the benchmark may load it.  It shares no code, header,
+ * table or constant generator with the CUDA library, and the CUDA library
+ * never calls it.
  *
  * Every step is written out in the plainest form that follows the paper:
  *   - nodal values by direct double sums over all modes (no sum factorisation),
