@@ -125,6 +125,22 @@ def test_step_parity_and_mass(nlon, nlat, p, seed, nsteps, prec):
     assert abs(gm1 / gm0 - 1) < (1e-13 if prec == "fp64" else 1e-9), (gm0, gm1)
 
 
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("p,nlon,nlat", SMALL)
+def test_step_parity_small_meshes(p, nlon, nlat, prec):
+    """Five SSP-RK3 steps on every degree and ragged / degenerate mesh: from
+    the second stage on each tile also stages its halo ring's increment
+    (16-, 8- or 4-byte pieces, by the size of an element's modes)."""
+    nsteps = 5
+    o, u = case(nlon, nlat, p, 11)
+    dt, m0, want = _oracle_run(nlon, nlat, p, 11, nsteps)
+    with solver(nlon, nlat, p, prec) as s:
+        s.set_state(u)
+        s.step(nsteps, dt)
+        got = s.get_state()
+    assert_within(state_err(got, want), TOL[prec], f"{nsteps} steps p={p} {nlon}x{nlat} {prec}")
+
+
 @pytest.mark.parametrize("order", [1, 2, 3, 4])
 def test_rk_orders(order):
     nlon, nlat, p = 16, 8, 2
