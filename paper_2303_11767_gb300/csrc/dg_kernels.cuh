@@ -231,10 +231,11 @@ __device__ __forceinline__ void store_row<double, 4>(double *p, const double *o)
 
 // Row of the stage state u_stage = base + inc (inc may be null).
 template <typename T, int N>
-__device__ __forceinline__ void load_stage_row(const T *__restrict__ base, const T *__restrict__ inc, size_t off, T *o)
+__device__ __forceinline__ void load_stage_row(const T *__restrict__ base, const T *__restrict__ inc, bool has_inc,
+                                               size_t off, T *o)
 {
     load_row<T, N>(base + off, o);
-    if (inc) {
+    if (has_inc) {
         T d[N];
         load_row<T, N>(inc + off, d);
 #pragma unroll
@@ -246,9 +247,16 @@ __device__ __forceinline__ void load_stage_row(const T *__restrict__ base, const
 // modes of the tile's halo ring reach shared memory through asynchronous
 // contiguous copies issued at the start of the tile, so that their latency
 // overlaps the tile's own S1 / S4 work.
-template <typename T, int N, int W>
+// INC / FIN fix at compile time whether the stage has an increment (A.inc)
+// and whether it is a step's final stage (A.out_base): 1 yes, 0 no, -1 read
+// from the arguments.
+template <typename T, int N, int W, int INC = -1, int FIN = -1>
 __device__ __forceinline__ void stage_tile(const StageArgs<T> &A, int bx, int by, unsigned char *smem_raw)
 {
+    const T *const incp = INC == 0 ? nullptr : A.inc;
+    const bool has_inc = INC == 0 ? false : INC == 1 ? true : (A.inc != nullptr);
+    T *const outb = FIN == 0 ? nullptr : A.out_base;
+    const bool fin = FIN == 0 ? false : FIN == 1 ? true : (A.out_base != nullptr);
     using GE = Geo<N, W>;
     constexpr int G = GE::G, NP = GE::NP, EL = GE::EL, SA = GE::SA, WB = GE::WB;
     constexpr int TW = GE::TW, TRC = GE::TRC;
@@ -282,7 +290,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &A, int bx, int by
     T uh[3][N];
 #pragma unroll
     for (int f = 0; f < 3; ++f) {
-        if (valid) load_stage_row<T, N>(A.base, A.inc, e * EL + f * NP + k * N, uh[f]);
+        if (valid) load_stage_row<T, N>(A.base, incp, has_inc, e * EL + f * NP + k * N, uh[f]);
         else {
 #pragma unroll
             for (int a = 0; a < N; ++a) uh[f][a] = T(0);
@@ -319,7 +327,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &A, int bx, int by
             }
             const size_t o = ((size_t)hj * A.nlon + hi) * EL + c;
             cp_async<SM::CP>(ef + h * EL + c, A.base + o);
-            if (A.inc) cp_async<SM::CP>(ef + GE::HALO_CAP + h * EL + c, A.inc + o);
+            if (has_inc) cp_async<SM::CP>(ef + GE::HALO_CAP + h * EL + c, incp + o);
         }
     }
 
@@ -328,7 +336,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &A, int bx, int by
 #pragma unroll
         for (int f = 0; f < 3; ++f) {
             const size_t off = e * EL + f * NP + k * N;
-            if (A.out_base) asm volatile("prefetch.global.L1 [%0];" ::"l"(A.base + off));
+            if (fin) asm volatile("prefetch.global.L1 [%0];" ::"l"(A.base + off));
             if (A.lo) asm volatile("prefetch.global.L1 [%0];" ::"l"(A.lo + off));
             if (A.acc_in) asm volatile("prefetch.global.L1 [%0];" ::"l"(A.acc_in + off));
         }
@@ -423,7 +431,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &A, int bx, int by
                 const T *hb = ef + hh * EL + f * NP + b * N;
 #pragma unroll
                 for (int a = 0; a < N; ++a) row[a] = hb[a];
-                if (A.inc) {
+                if (has_inc) {
 #pragma unroll
                     for (int a = 0; a < N; ++a) row[a] += hb[GE::HALO_CAP + a];
                 }
@@ -652,7 +660,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &A, int bx, int by
                     if (!isfinite(kk[f][a])) st |= DG_STATUS_NONFINITE;
                 if (A.out_rhs) store_row<T, N>(A.out_rhs + off, kk[f]);
                 T inc[N];
-                if (A.inc) load_row<T, N>(A.inc + off, inc);
+                if (has_inc) load_row<T, N>(incp + off, inc);
                 else {
 #pragma unroll
                     for (int a = 0; a < N; ++a) inc[a] = T(0);
@@ -675,7 +683,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &A, int bx, int by
                     for (int a = 0; a < N; ++a) o[a] = fma(adt, kk[f][a], acc[a]);
                     store_row<T, N>(A.acc_out + off, o);
                 }
-                if (A.out_base) {
+                if (fin) {
                     // u^{n+1} = (base + lo) + delta with an error-free two-sum,
                     // so increments far below one ulp of the state survive
                     T bs[N], lo[N], ob[N], ol[N];
@@ -717,7 +725,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &A, int bx, int by
                         ol[a] = l1 - (hi - s1);
                         if (!isfinite(hi)) st |= DG_STATUS_NONFINITE;
                     }
-                    store_row<T, N>(A.out_base + off, ob);
+                    store_row<T, N>(outb + off, ob);
                     if (A.out_lo) store_row<T, N>(A.out_lo + off, ol);
                 }
             }
@@ -726,12 +734,12 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &A, int bx, int by
     if (st && valid) atomicOr(A.status, st);
 }
 
-template <typename T, int N, int W>
+template <typename T, int N, int W, int INC, int FIN>
 __global__ void __launch_bounds__(32 * W) stage_kernel(const StageArgs<T> A)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     pdl_wait();
-    stage_tile<T, N, W>(A, blockIdx.x, blockIdx.y, smem_raw);
+    stage_tile<T, N, W, INC, FIN>(A, blockIdx.x, blockIdx.y, smem_raw);
     pdl_launch_dependents();
 }
 
@@ -747,18 +755,33 @@ int launch_stage_n(const StageArgs<T> &a, cudaStream_t s)
     constexpr int W = DG_WARPS;
     using GE = Geo<N, W>;
     const size_t smem = stage_smem_bytes<T, N, W>();
+    // One kernel per stage kind (increment present or not, final stage or
+    // not) up to p = 3, where the specialised kernels measured faster
+    // (180x90: 6.28 -> 5.98 us per stage); one kernel reading the kind from
+    // its arguments at p = 4, where they did not (360x180: 43.2 -> 44.2 us).
+    using K = void (*)(const StageArgs<T>);
+    K k00, k01, k10, k11;
+    if constexpr (N <= 4) {
+        k00 = stage_kernel<T, N, W, 0, 0>;
+        k01 = stage_kernel<T, N, W, 0, 1>;
+        k10 = stage_kernel<T, N, W, 1, 0>;
+        k11 = stage_kernel<T, N, W, 1, 1>;
+    } else {
+        k00 = k01 = k10 = k11 = stage_kernel<T, N, W, -1, -1>;
+    }
     // the shared-memory opt-in is a per-device function attribute
     static unsigned long long attr_set = 0;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 1;
     if (!(attr_set >> dev & 1ull)) {
-        if (cudaFuncSetAttribute(stage_kernel<T, N, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-            cudaSuccess)
-            return 1;
+        for (K k : {k00, k01, k10, k11})
+            if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+                return 1;
         attr_set |= 1ull << dev;
     }
     dim3 grid((a.nlon + GE::G - 1) / GE::G, (a.nlat + W - 1) / W);
-    if (launch_pdl(stage_kernel<T, N, W>, grid, dim3(32 * W), smem, s, a) != cudaSuccess) return 1;
+    const K k = a.inc ? (a.out_base ? k11 : k10) : (a.out_base ? k01 : k00);
+    if (launch_pdl(k, grid, dim3(32 * W), smem, s, a) != cudaSuccess) return 1;
     return cudaPeekAtLastError() == cudaSuccess ? 0 : 1;
 }
 
