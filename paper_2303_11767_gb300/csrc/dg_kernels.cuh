@@ -24,6 +24,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <atomic>
 #include <cstdint>
 #include <type_traits>
 
@@ -770,14 +771,14 @@ int launch_stage_n(const StageArgs<T> &a, cudaStream_t s)
         k00 = k01 = k10 = k11 = stage_kernel<T, N, W, -1, -1>;
     }
     // the shared-memory opt-in is a per-device function attribute
-    static unsigned long long attr_set = 0;
+    static std::atomic<unsigned long long> attr_set{0};   // handles on other host threads may launch too
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 1;
-    if (!(attr_set >> dev & 1ull)) {
+    if (!(attr_set.load(std::memory_order_acquire) >> dev & 1ull)) {
         for (K k : {k00, k01, k10, k11})
             if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
                 return 1;
-        attr_set |= 1ull << dev;
+        attr_set.fetch_or(1ull << dev, std::memory_order_release);   // setting it twice is harmless
     }
     dim3 grid((a.nlon + GE::G - 1) / GE::G, (a.nlat + W - 1) / W);
     const K k = a.inc ? (a.out_base ? k11 : k10) : (a.out_base ? k01 : k00);
@@ -852,14 +853,14 @@ template <typename T, int W>
 int launch_ensemble_w(int grid, const EnsArgs<T> &a, cudaStream_t s)
 {
     const size_t smem = ensemble_smem_bytes<T, W>();
-    static unsigned long long attr_set = 0;
+    static std::atomic<unsigned long long> attr_set{0};   // handles on other host threads may launch too
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 1;
-    if (!(attr_set >> dev & 1ull)) {
+    if (!(attr_set.load(std::memory_order_acquire) >> dev & 1ull)) {
         if (cudaFuncSetAttribute(ensemble_kernel<T, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
             cudaSuccess)
             return 1;
-        attr_set |= 1ull << dev;
+        attr_set.fetch_or(1ull << dev, std::memory_order_release);   // setting it twice is harmless
     }
     ensemble_kernel<T, W><<<grid, 32 * W, smem, s>>>(a);
     return cudaPeekAtLastError() == cudaSuccess ? 0 : 1;

@@ -27,6 +27,7 @@
 
 #include <cstdint>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "dg_internal.h"
@@ -881,12 +882,16 @@ void build_tables(std::vector<uint16_t> &b1, std::vector<uint16_t> &b2)
 struct TabSet {
     uint4 *b1 = nullptr, *b2 = nullptr;
 };
+// per device, degree and operand type: the basis operands and whether the
+// shared-memory opt-in is set; handles on several host threads share them,
+// so every access holds g_tc_mu
+std::mutex g_tc_mu;
 TabSet g_tabs[64][DG_MAXN][2];
 unsigned long long g_attr[DG_MAXN][2];
 unsigned long long g_check_attr[DG_MAXN][2];
 
 template <int N, typename OpT>
-int tables_for(int dev, int op, TabSet &out)
+int tables_for(int dev, int op, TabSet &out)   // caller holds g_tc_mu
 {
     TabSet &t = g_tabs[dev][N - 1][op];
     if (!t.b1) {
@@ -919,6 +924,7 @@ int prepare_tc(int op, TabSet &t)
     using SM = TcSmem<N>;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 1;
+    std::lock_guard<std::mutex> lock(g_tc_mu);
     if (tables_for<N, OpT>(dev, op, t)) return 1;
     if (!(g_attr[N - 1][op] >> dev & 1ull)) {
         if (cudaFuncSetAttribute(tc_stage_kernel<N, OpT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -935,8 +941,12 @@ int launch_tc(int op, const StageArgs<float> &a, cudaStream_t s)
     using SM = TcSmem<N>;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 1;
-    const TabSet t = g_tabs[dev][N - 1][op];
-    if (!t.b1 || !(g_attr[N - 1][op] >> dev & 1ull)) return 1;   // dg_prepare_stage_tc was not called
+    TabSet t;
+    {
+        std::lock_guard<std::mutex> lock(g_tc_mu);
+        t = g_tabs[dev][N - 1][op];
+        if (!t.b1 || !(g_attr[N - 1][op] >> dev & 1ull)) return 1;   // dg_prepare_stage_tc was not called
+    }
     dim3 grid((a.nlon + TC_TW - 1) / TC_TW, (a.nlat + 3) / 4);
     if (dgk::launch_pdl(tc_stage_kernel<N, OpT>, grid, dim3(128 * TC_TPE), SM::BYTES, s, a,
                         (const uint4 *)t.b1, (const uint4 *)t.b2) != cudaSuccess)
@@ -954,13 +964,16 @@ int check_tc(int op, const float *a, float *d, int *n1, int *k1, cudaStream_t s)
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 1;
     TabSet t;
-    if (tables_for<N, OpT>(dev, op, t)) return 1;
     constexpr uint32_t bytes = (GE::N1 * GE::K1 * 2 + 1023) / 1024 * 1024 + GE::K1C * CH;
-    if (!(g_check_attr[N - 1][op] >> dev & 1ull)) {
-        if (cudaFuncSetAttribute(tc_gemm_check_kernel<N, OpT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)bytes) != cudaSuccess)
-            return 1;
-        g_check_attr[N - 1][op] |= 1ull << dev;
+    {
+        std::lock_guard<std::mutex> lock(g_tc_mu);
+        if (tables_for<N, OpT>(dev, op, t)) return 1;
+        if (!(g_check_attr[N - 1][op] >> dev & 1ull)) {
+            if (cudaFuncSetAttribute(tc_gemm_check_kernel<N, OpT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)bytes) != cudaSuccess)
+                return 1;
+            g_check_attr[N - 1][op] |= 1ull << dev;
+        }
     }
     unsigned *st = nullptr;
     if (cudaMallocAsync(&st, sizeof(unsigned), s) != cudaSuccess) return 1;
