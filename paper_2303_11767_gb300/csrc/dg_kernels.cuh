@@ -8,8 +8,10 @@
 //   S1  modal -> Gauss-point values, sum-factorised (a-pass, then b-pass)
 //   S2  pointwise fluxes F, G and sources S with cos/sin(theta) row tables
 //   S3  volume integral, sum-factorised (beta-pass, then alpha-pass)
-//   S4  edge traces of the element; the tile's halo ring computes the traces
-//       its neighbours need, so no second pass over memory is made
+//   S4  edge traces of the element; the modes of the tile's halo ring are
+//       copied into shared memory (asynchronous copies issued at the start
+//       of the tile) and the ring's traces computed from them, so no second
+//       pass over memory is made
 //   S5  Rusanov flux (Eq. rusanov) at every edge point, zero at pole edges
 //   S6  lift of the edge fluxes
 //   S7  inverse of the per-row cos(theta)-weighted mass matrix
@@ -20,7 +22,9 @@
 // latitude row; N lanes per element.  Lane k first owns row b = k of the modal
 // coefficients, then column alpha = k of the Gauss points (after a transpose
 // through shared memory), then row b = k again for the output.  A block of
-// DG_WARPS warps covers G x DG_WARPS elements.
+// DG_WARPS warps covers G x DG_WARPS elements.  Up to p = 3 there is one
+// kernel per stage kind (increment or not, final stage or not) and the FP32
+// contractions run on paired FP32 instructions.
 #pragma once
 
 #include <cuda_runtime.h>
