@@ -1,13 +1,22 @@
 """Benchmark of the fused DG shallow-water stage on one GB300 (or N replicas).
 
 Metric: DOF-updates/s per RK stage (DOF = 3 (p+1)^2 nlon nlat, one update per
-DOF per Runge-Kutta stage).  One bench step is the workload of the 180 x 90,
-degree 3 configuration: 1000 SSP-RK3 time steps (3000 fused stage kernels,
-replayed from one captured CUDA graph) plus the compensated mass reduction,
-on the seeded synthetic field (depth 5960 m + 200 m of random spherical
+DOF per Runge-Kutta stage).  One bench step is the workload of the 360 x 180,
+degree 4 configuration: 500 SSP-RK3 time steps (1500 fused stage kernels,
+replayed from captured CUDA graphs) plus the compensated mass reduction, on
+the seeded synthetic field (depth 5960 m + 200 m of random spherical
 harmonics l <= 4, flow from a random stream function, |u| <= 20 m/s).  L2 is
 flushed (256 MiB write) before every timed step; each step is timed with CUDA
 events on the solver's stream.
+
+The state arrays of that mesh (19.4 MB each) stay in the 129 MB L2 across the
+stages of a step, so the roofline object of the line comes from a second,
+streaming leg on the 1440 x 720 degree-4 mesh (311 MB per array), timed the
+same way.  "At stated L2 error" is reported per field as (i) the deviation of
+each precision from the FP64 path on the same mesh and, over a bounded
+sample, from the FP64 oracle, and (ii) the FP64 discretisation error against
+the same run on the 2x refined mesh at degree 4, with the verdict
+"matches" = (i) <= 0.1 (ii).
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 Under torchrun each rank runs an independent replica (weak scaling).
@@ -59,7 +68,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS) + ["c4"])
+    ap.add_argument("--workload", default="c3", choices=sorted(WORKLOADS) + ["c4"])
     ap.add_argument("--precision", default="fp32", choices=sorted(DTYPES))
     ap.add_argument("--rk-steps", type=int, default=0, help="override RK steps per bench step")
     ap.add_argument("--no-extras", action="store_true", help="skip fp64-plain, e2e and cpu legs (profiling)")
@@ -289,18 +298,14 @@ def run_reference(args, world, rank):
     }))
 
 
-def member_means(nlon, nlat, p, seed, radius):
-    """Element means (mode 0) of member k's seeded field."""
-    from paper_2303_11767_gb300 import synth
+def member_state(nlon, nlat, p, seed):
+    """Member k's own seeded field, projected onto its modal basis (the
+    library's cos(theta)-weighted projection, through a temporary FP64
+    handle of the member's mesh)."""
+    from paper_2303_11767_gb300 import dgswe, synth
 
-    field = synth.SmoothField(seed, radius)
-    lam = (np.arange(nlon) + 0.5) * (2 * math.pi / nlon)
-    th = -0.5 * math.pi + (np.arange(nlat) + 0.5) * (math.pi / nlat)
-    n = p + 1
-    u = np.zeros((nlat, nlon, 3, n * n))
-    for f, v in enumerate(field.fields_grid(lam, th)):
-        u[:, :, f, 0] = 2.0 * v
-    return u
+    with dgswe.Solver(nlon, nlat, p, precision="fp64") as sv:
+        return sv.project_grid(synth.SmoothField(seed, sv.radius).fields_grid)
 
 
 def run_ensemble(args, world, rank, local):
@@ -316,8 +321,10 @@ def run_ensemble(args, world, rank, local):
     nsteps = args.rk_steps or 10
     nlon, nlat, deg = synth.ensemble_members(256)
     e = dgswe.Ensemble(nlon, nlat, deg)
+    t_init = time.perf_counter()
     for k in range(e.members):
-        e.set_state(k, member_means(nlon[k], nlat[k], deg[k], synth.ensemble_member_seed(k), e.radius))
+        e.set_state(k, member_state(nlon[k], nlat[k], deg[k], synth.ensemble_member_seed(k)))
+    t_init = time.perf_counter() - t_init
     e.set_dt([e.max_dt(k, CFL) for k in range(e.members)])
     e.set_option(dgswe.OPT_STREAM, stream.cuda_stream)
     e.set_option(dgswe.OPT_STEPS_PER_GRAPH, nsteps)
@@ -351,7 +358,7 @@ def run_ensemble(args, world, rank, local):
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": ENSEMBLE_DESC, "members": e.members, "dof": dof, "rk_steps_per_step": nsteps,
                    "tile_rows": tile_rows, "blocks_per_sm": bps, "autotune_ms_per_step": tuned_ms,
-                   "init": "element means of each member's seeded field", "cfl": CFL,
+                   "init": f"each member's own seeded field, projected ({t_init:.0f} s on the host)", "cfl": CFL,
                    "l2": "inputs (1.07 GB per state array) exceed L2; flushed before every timed step"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": None, "peak_kind": peak_kind, "kernel": "ensemble_kernel<fp32>",
@@ -361,6 +368,105 @@ def run_ensemble(args, world, rank, local):
     }
     if rank == 0:
         print(json.dumps(out))
+
+
+def prolong(u, r, nf):
+    """Modal state of a mesh refined r x r with nf points per direction that
+    represents the coarse state exactly (every coarse polynomial restricted to
+    a sub-element is a polynomial of degree <= nf - 1 there): per direction
+    the transfer T[s][a_f][a_c] = int L_af(x) L_ac((x + 2s + 1)/r - 1) dx,
+    exact with an nf-point Gauss rule.  u: [nlat, nlon, 3, nc^2]."""
+    from numpy.polynomial import legendre as npleg
+
+    nlat, nlon, nfld, ncp = u.shape
+    nc = int(round(math.sqrt(ncp)))
+    x, w = npleg.leggauss(max(nf, nc) + 1)
+
+    def L(k, t):
+        c = np.zeros(k + 1)
+        c[k] = 1.0
+        return math.sqrt((2 * k + 1) / 2.0) * npleg.legval(t, c)
+
+    T = np.array([[[np.sum(w * L(af, x) * L(ac, (x + 2 * sub + 1) / r - 1)) for ac in range(nc)] for af in range(nf)]
+                  for sub in range(r)])                                   # [r][nf][nc]
+    uc = u.reshape(nlat, nlon, nfld, nc, nc)                              # [j][i][f][b][a]
+    uf = np.einsum("yBb,xAa,jifba->jyixfBA", T, T, uc)                   # [j][sy][i][sx][f][B][A]
+    return np.ascontiguousarray(uf.reshape(nlat * r, nlon * r, nfld, nf * nf))
+
+
+def accuracy_leg(name, precisions, make64, make_prec, log=None):
+    """(i) and (ii) of "at stated L2 error" for one workload, per field:
+    (ii) = relative L2 of the FP64 state after the workload's steps against
+    the FP64 run of the same initial state, prolonged exactly onto the 2x
+    refined mesh at degree 4 and advanced to the same time with its own CFL
+    step, then projected back (the library's nested cos(theta)-weighted
+    projection); (i) = relative L2 of each precision against the FP64 state
+    on the same mesh.  A precision matches where (i) <= 0.1 (ii)."""
+    nlon, nlat, p, nsteps, seed, desc = WORKLOADS[name]
+    s64 = make64(nlon, nlat, p)
+    u0 = initial_state(s64, seed)
+    s64.set_state(u0)
+    dt = s64.max_dt(CFL)
+    T = nsteps * dt
+    s64.step(nsteps, dt)
+    u64 = s64.get_state()
+    t0 = time.perf_counter()
+    fine = make64(2 * nlon, 2 * nlat, 4)
+    fine.set_state(prolong(u0, 2, 5))
+    dtf = fine.max_dt(CFL)
+    mf = int(math.ceil(T / dtf))
+    fine.step(mf, T / mf)
+    back = make64(nlon, nlat, p)
+    back.restrict_from(fine)
+    ref = back.get_state()
+    ref_s = time.perf_counter() - t0
+    for x in (fine, back, s64):
+        x.close()
+    ii = field_errors(u64, ref)
+    out = {"workload": desc, "T_s": T, "steps": nsteps,
+           "reference": f"FP64 on {2 * nlon}x{2 * nlat} degree 4 ({mf} steps of {T / mf:.3e} s, "
+                        f"{ref_s:.1f} s), prolonged initial state, nested projection back",
+           "fields": ["h", "hu", "hv"], "ii_fp64_discretisation": ii, "i_vs_fp64": {}, "matches": {}}
+    for prec in precisions:
+        sv = make_prec(nlon, nlat, p, prec)
+        sv.set_state(u0)
+        sv.step(nsteps, dt)
+        e = field_errors(sv.get_state(), u64)
+        sv.close()
+        out["i_vs_fp64"][prec] = e
+        out["matches"][prec] = [bool(a <= 0.1 * b) for a, b in zip(e, ii)]
+    return out
+
+
+def streaming_leg(prec, torch, stream, flush, make_prec, reps=3, nsteps=20):
+    """Per-launch time of the stage kernel on the 1440 x 720 degree-4 mesh,
+    whose state arrays (311 MB each in FP32) stream from HBM every stage:
+    CUDA events around graph replays of nsteps SSP-RK3 steps, L2 flushed
+    before each; the mean launch time over all launches of the timed reps."""
+    nlon, nlat, p, _, seed, desc = WORKLOADS["r1"]
+    s = make_prec(nlon, nlat, p, prec, nsteps)
+    s.set_state(initial_state(s, seed))
+    dt = s.max_dt(CFL)
+    l0 = s.stage_launches()
+    ms = []
+    with torch.cuda.stream(stream):
+        for it in range(1 + reps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            s.step(nsteps, dt)
+            b.record(stream)
+            b.synchronize()
+            if it:
+                ms.append(a.elapsed_time(b))
+    launches = (s.stage_launches() - l0) * reps // (reps + 1)
+    s.close()
+    dof = 3 * (p + 1) ** 2 * nlon * nlat
+    launch_s = sum(ms) * 1e-3 / launches
+    bpl = dof * 4 * 8.0 / 3.0
+    return {"workload": desc, "dof": dof, "launch_us": launch_s * 1e6, "bytes_per_launch": bpl,
+            "achieved": bpl / launch_s / 1e9, "value": dof / launch_s, "launches": launches,
+            "kernel": KERNELS[prec].format(n=p + 1)}
 
 
 def main():
@@ -386,11 +492,14 @@ def main():
     flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     mass_t = torch.zeros(1, dtype=torch.float64, device="cuda")
 
+    def make_mesh(nx, ny, pp, prec, steps_per_graph):
+        sv = dgswe.Solver(nx, ny, pp, precision=prec, check_finite=False)
+        sv.set_option(dgswe.OPT_STREAM, stream.cuda_stream)
+        sv.set_option(dgswe.OPT_STEPS_PER_GRAPH, min(max(steps_per_graph, 1), 1024))
+        return sv
+
     def make(prec):
-        s = dgswe.Solver(nlon, nlat, p, precision=prec, check_finite=False)
-        s.set_option(dgswe.OPT_STREAM, stream.cuda_stream)
-        s.set_option(dgswe.OPT_STEPS_PER_GRAPH, min(nsteps, 1024))
-        return s
+        return make_mesh(nlon, nlat, p, prec, nsteps)
 
     s = make(args.precision)
     u0 = initial_state(s, seed)
@@ -413,7 +522,7 @@ def main():
     s.step(1, dt)                                          # raises if any stage met NaN / h <= 0
     ms_per_step = total_ms / args.steps
 
-    # dominant kernel: the fused stage; algorithmic bytes per launch = the mean
+    # the fused stage on this workload; algorithmic bytes per launch = the mean
     # 8/3 state words per DOF of SSP-RK3 (u read by all stages, u^n by two, one write)
     word = 8 if args.precision == "fp64" else 4
     bytes_per_launch = dof * word * 8.0 / 3.0
@@ -421,11 +530,11 @@ def main():
     peak, peak_kind = peaks()
     achieved = bytes_per_launch / launch_s / 1e9
     traffic = TRAFFIC.get((args.precision, args.workload))
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": traffic[0] if traffic else None,
-                "traffic_note": traffic[1] if traffic else "no capture of this kernel and workload",
-                "peak_kind": peak_kind, "kernel": KERNELS[args.precision].format(n=p + 1),
-                "bytes_per_launch": bytes_per_launch, "launch_us": launch_s * 1e6}
+    roofline_here = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": traffic[0] if traffic else None,
+                     "traffic_note": traffic[1] if traffic else "no capture of this kernel and workload",
+                     "peak_kind": peak_kind, "kernel": KERNELS[args.precision].format(n=p + 1),
+                     "bytes_per_launch": bytes_per_launch, "launch_us": launch_s * 1e6, "workload": desc}
 
     out = {
         "metric": METRIC, "value": value, "unit": "DOF-updates/s", "n_gpus": world, "steps": args.steps,
@@ -434,20 +543,45 @@ def main():
         "config": {"workload": desc, "nlon": nlon, "nlat": nlat, "degree": p, "dof": dof,
                    "rk_steps_per_step": nsteps, "dt": dt, "cfl": CFL, "l2": "flushed before every timed step",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
-        "roofline": roofline,
+        "roofline": roofline_here,
         # + the two mass kernels per step; the tensor-core path also permutes
         # u^n (base and low parts) into and out of its lane-contiguous layout
+        # once per graph of up to 1024 steps
         "gpu_launches": stage_launches_timed + (6 if "tc" in args.precision else 2) * args.steps,
         "clocks": clk.summary(),
         "mass_drift": (m1 - m0) / m0,
     }
 
     if not args.no_extras and rank == 0 and world == 1:
+        def make_prec(nx, ny, pp, prec, steps_per_graph=64):
+            return make_mesh(nx, ny, pp, prec, steps_per_graph)
+
+        # ---- the roofline: the same kernel on the mesh that streams from HBM
+        if args.workload != "r1" and args.precision != "fp64":
+            leg = streaming_leg(args.precision, torch, stream, flush, make_prec)
+            tr = TRAFFIC.get((args.precision, "r1"))
+            out["roofline"] = {"bound": "hbm", "achieved": leg["achieved"], "peak": peak, "unit": "GB/s",
+                               "frac": leg["achieved"] / peak, "traffic": tr[0] if tr else None,
+                               "traffic_note": tr[1] if tr else "no capture of this kernel and workload",
+                               "peak_kind": peak_kind, "kernel": leg["kernel"],
+                               "bytes_per_launch": leg["bytes_per_launch"], "launch_us": leg["launch_us"],
+                               "workload": leg["workload"], "value": leg["value"]}
+            out["roofline_timed_workload"] = dict(roofline_here, note="state arrays L2-resident across stages")
+            for tcp in ("fp32", "fp32_tc_bf16", "fp32_tc_fp16"):
+                if tcp != args.precision:
+                    lv = streaming_leg(tcp, torch, stream, flush, make_prec)
+                    tr = TRAFFIC.get((tcp, "r1"))
+                    out.setdefault("roofline_variants", {})[tcp] = {
+                        "achieved": lv["achieved"], "frac": lv["achieved"] / peak, "launch_us": lv["launch_us"],
+                        "value": lv["value"], "kernel": lv["kernel"], "traffic": tr[0] if tr else None,
+                        "workload": lv["workload"]}
+
         # ---- FP64 plain path on the same workload
         s64 = make("fp64")
         s64.set_state(u0)
         k64 = max(2, args.steps // 5)
         t64 = time_device(s64, torch, stream, nsteps, dt, k64, 1, mass_t, flush)
+        s64.close()
         v64 = dof * 3 * nsteps * k64 / (sum(t64) * 1e-3)
         fp64_peak = dgswe.measure_fp64_peak(5)
         fpd = stage_flops_per_dof(p + 1)
@@ -457,6 +591,32 @@ def main():
                                           "unit": "GFLOP/s", "frac": v64 * fpd / 1e9 / fp64_peak,
                                           "peak_kind": "measured FP64 FMA probe (dg_measure_fp64_peak)",
                                           "flops_per_dof": fpd}}
+
+        # ---- the tensor-core precisions on the same workload (device-timed)
+        for tcp in ("fp32", "fp32_tc_bf16", "fp32_tc_fp16"):
+            if tcp == args.precision:
+                continue
+            stc = make(tcp)
+            stc.set_state(u0)
+            ktc = max(2, args.steps // 5)
+            ttc = time_device(stc, torch, stream, nsteps, dt, ktc, 1, mass_t, flush)
+            stc.close()
+            vtc = dof * 3 * nsteps * ktc / (sum(ttc) * 1e-3)
+            out.setdefault("variants", {})[tcp] = {"value": vtc, "ms_per_step": sum(ttc) / ktc,
+                                                   "dtype": DTYPES[tcp], "steps": ktc,
+                                                   "kernel": KERNELS[tcp].format(n=p + 1)}
+
+        # ---- the 180 x 90 degree-3 workload, FP32 (kept beside the headline)
+        if args.workload != "c2":
+            n2, l2_, p2, ns2, sd2, desc2 = WORKLOADS["c2"]
+            sc2 = make_mesh(n2, l2_, p2, "fp32", ns2)
+            sc2.set_state(initial_state(sc2, sd2))
+            dt2 = sc2.max_dt(CFL)
+            t2 = time_device(sc2, torch, stream, ns2, dt2, max(2, args.steps // 5), 1, mass_t, flush)
+            sc2.close()
+            dof2 = 3 * (p2 + 1) ** 2 * n2 * l2_
+            out["workload_c2"] = {"workload": desc2, "value": dof2 * 3 * ns2 * len(t2) / (sum(t2) * 1e-3),
+                                  "dtype": "f32", "ms_per_step": sum(t2) / len(t2)}
 
         # ---- the paper's own timing workload (planar geostrophic adjustment,
         #      50x50 elements, 360 RK4 steps of 100 s), FP64 planar kernel, with
@@ -490,19 +650,6 @@ def main():
                                  "unit": "DOF-updates/s", "paper_hardware": "12-core Xeon E5-2690 v3 (CPU only; "
                                  "throughput derived from its total-time table)", **legs}
 
-        # ---- the tensor-core precisions on the same workload (device-timed)
-        for tcp in ("fp32_tc_bf16", "fp32_tc_fp16"):
-            if tcp == args.precision:
-                continue
-            stc = make(tcp)
-            stc.set_state(u0)
-            ktc = max(2, args.steps // 5)
-            ttc = time_device(stc, torch, stream, nsteps, dt, ktc, 1, mass_t, flush)
-            vtc = dof * 3 * nsteps * ktc / (sum(ttc) * 1e-3)
-            out.setdefault("variants", {})[tcp] = {"value": vtc, "ms_per_step": sum(ttc) / ktc,
-                                                   "dtype": DTYPES[tcp], "steps": ktc,
-                                                   "kernel": KERNELS[tcp].format(n=p + 1)}
-
         # ---- end to end through the C-ABI with pinned host buffers
         hin = torch.empty(s.state_len, dtype=torch.float64, pin_memory=True).numpy()
         hout = torch.empty(s.state_len, dtype=torch.float64, pin_memory=True).numpy()
@@ -518,9 +665,19 @@ def main():
             mass = se.total_mass()
             hout[:] = se.get_state().reshape(-1)
         e2e_s = time.perf_counter() - t0
+        se.close()
         out["e2e"] = {"value": dof * 3 * nsteps * args.steps / e2e_s, "unit": "DOF-updates/s",
                       "h2d_bytes_per_step": int(hin.nbytes), "d2h_bytes_per_step": int(hout.nbytes) + 8,
                       "ms_per_step": 1e3 * e2e_s / args.steps, "mass": mass}
+
+        # ---- at stated L2 error: (i) and (ii) on this workload and on 180x90 p = 3
+        precs = ["fp32", "fp32_tc_bf16", "fp32_tc_fp16"]
+        acc = {args.workload: accuracy_leg(args.workload, precs, lambda a, b, c: make_mesh(a, b, c, "fp64", 256),
+                                           lambda a, b, c, d: make_mesh(a, b, c, d, 256))}
+        if args.workload != "c2":
+            acc["c2"] = accuracy_leg("c2", precs, lambda a, b, c: make_mesh(a, b, c, "fp64", 256),
+                                     lambda a, b, c, d: make_mesh(a, b, c, d, 256))
+        out["at_l2_error"] = acc
 
         # ---- the oracle on the host cores (bounded sample) and the L2 error
         leg = cpu_leg(nlon, nlat, p, seed, budget_s=15.0, max_steps=nsteps)
@@ -542,6 +699,7 @@ def main():
             sv.set_state(leg["u0"])
             sv.step(leg["nsteps"], leg["dt"])
             errs[prec] = field_errors(sv.get_state(), leg["u1"])
+            sv.close()
         out["l2_error_vs_oracle"] = {"steps": leg["nsteps"], "fields": ["h", "hu", "hv"], **errs}
     if rank == 0:
         print(json.dumps(out))

@@ -301,14 +301,18 @@ long long dg_ensemble_stage_launches(dg_ensemble e);
  * of DG_NOALLOC_MAX_NLAT + 1 64-bit words (64 KiB) inside the library, which
  * every GPU that loads the library holds until the process exits.  Meshes with
  * more than DG_NOALLOC_MAX_NLAT latitude rows are rejected with DG_EINVAL.
- * The result, dt = cfl H / (max(p,1) c) as for dg_max_dt, or -1 if h <= 0 or
- * NaN at a Gauss point, is written to the device double *d_dt; the work is
- * enqueued on `stream` (a cudaStream_t, NULL = the default stream) and the
- * call returns without waiting.  The first call on a device sets that device
- * up (finds the scratch array's device address and copies a small basis table
- * to constant memory), so make it before any stream capture begins.  All calls
- * share the one scratch array and each call overwrites it: calls whose work
- * overlaps on the GPU (unordered streams) race and can return wrong values. */
+ * The result, dt = cfl H / (max(p,1) c) as for dg_max_dt, or -1 if at some
+ * Gauss point h <= 0, h is NaN, or the wave speed is not finite (a NaN or Inf
+ * in hu or hv), is written to the device double *d_dt; the work is enqueued on
+ * `stream` (a cudaStream_t, NULL = the default stream) and the call returns
+ * without waiting.  The first call on a device sets that device up (finds the
+ * scratch array's device address and copies a small basis table to constant
+ * memory; host threads making that first call together are serialised), so
+ * make it before any stream capture begins.  The set-up is kept for the life
+ * of the process: after cudaDeviceReset of a device, do not call this entry
+ * point on that device again.  All calls share the one scratch array and each
+ * call overwrites it: calls whose work overlaps on the GPU (unordered streams)
+ * race and can return wrong values. */
 #define DG_NOALLOC_MAX_NLAT 8192
 dg_status dg_max_dt_noalloc(const double *d_modal, int nlon, int nlat, int degree, double radius, double g,
                             double cfl, double *d_dt, void *stream);

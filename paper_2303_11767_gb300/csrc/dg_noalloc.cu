@@ -14,6 +14,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 
 #include "dg_internal.h"
 #include "../../include/dgswe.h"
@@ -55,7 +56,11 @@ __global__ void noalloc_row_speed(const double *__restrict__ u, int nlon, double
                 const double h = qv[0];
                 if (!(h > 0.0)) { bad = 1; continue; }
                 const double uu = qv[1] / h, vv = qv[2] / h;
-                best = fmax(best, sqrt(uu * uu + vv * vv) + sqrt(g * h));
+                const double sp = sqrt(uu * uu + vv * vv) + sqrt(g * h);
+                // a NaN or Inf in hu or hv makes the speed non-finite, and
+                // fmax would silently drop it
+                if (!isfinite(sp)) { bad = 1; continue; }
+                best = fmax(best, sp);
             }
     }
     __shared__ double red[32];
@@ -71,7 +76,8 @@ __global__ void noalloc_row_speed(const double *__restrict__ u, int nlon, double
 }
 
 // Single block: maximum over the rows, then dt = cfl H / (max(p,1) c);
-// writes -1 when some Gauss point had h <= 0 (or NaN).
+// writes -1 when some Gauss point had h <= 0, a NaN depth or a non-finite
+// wave speed (a NaN or Inf in hu or hv).
 __global__ void noalloc_finish(const unsigned long long *__restrict__ scratch, int nlat, int status_slot,
                                double cfl_H_over_p, double *__restrict__ dt_out)
 {
@@ -91,19 +97,35 @@ __global__ void noalloc_finish(const unsigned long long *__restrict__ scratch, i
 
 // Per-device set-up: the device address of the scratch array and the basis
 // table, done once per device on the first call (with that device current).
+// Host threads that make their first call on the same device at the same
+// time are serialised by g_setup_mu, so none of them can see the device
+// marked done before its scratch address is stored.  The cached address
+// belongs to the device's primary context: after cudaDeviceReset on that
+// device the module is loaded again and the address (and the constant basis
+// table) must be set up anew, which this file does not detect; a process
+// that resets a device must not call dg_max_dt_noalloc on it afterwards.
 struct DeviceSetup {
     bool done = false;
     unsigned long long *scratch = nullptr;
 };
 DeviceSetup g_setup[64];
+std::mutex g_setup_mu;
 
-dg_status setup_device(int dev, unsigned long long **scratch)
+dg_status setup_device(int dev, unsigned long long **scratch, const char **why)
 {
-    if (dev < 0 || dev >= 64) return DG_EINVAL;
+    if (dev < 0 || dev >= 64) {
+        *why = "device index outside the 64 devices this entry point supports";
+        return DG_EINVAL;
+    }
+    std::lock_guard<std::mutex> lock(g_setup_mu);
     DeviceSetup &s = g_setup[dev];
     if (!s.done) {
         void *ptr = nullptr;
-        if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess) return DG_ECUDA;
+        cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+        if (e != cudaSuccess) {
+            *why = cudaGetErrorString(e);
+            return DG_ECUDA;
+        }
         double lv[DG_MAXN][DG_MAXN][DG_MAXN];
         std::memset(lv, 0, sizeof lv);
         for (int n = 1; n <= DG_MAXN; ++n) {
@@ -112,7 +134,11 @@ dg_status setup_device(int dev, unsigned long long **scratch)
             for (int a = 0; a < n; ++a)
                 for (int q = 0; q < n; ++q) lv[n - 1][a][q] = dg_legendre(a, x[q]);
         }
-        if (cudaMemcpyToSymbol(c_na_LV, lv, sizeof lv) != cudaSuccess) return DG_ECUDA;
+        e = cudaMemcpyToSymbol(c_na_LV, lv, sizeof lv);
+        if (e != cudaSuccess) {
+            *why = cudaGetErrorString(e);
+            return DG_ECUDA;
+        }
         s.scratch = static_cast<unsigned long long *>(ptr);
         s.done = true;
     }
@@ -144,7 +170,8 @@ extern "C" dg_status dg_max_dt_noalloc(const double *d_modal, int nlon, int nlat
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return noalloc_fail(DG_ECUDA, "no CUDA device");
     unsigned long long *scratch = nullptr;
-    if (dg_status st = setup_device(dev, &scratch)) return noalloc_fail(st, cudaGetErrorString(cudaGetLastError()));
+    const char *why = "";
+    if (dg_status st = setup_device(dev, &scratch, &why)) return noalloc_fail(st, why);
     // H = min over rows and Gauss points of min(R dth, R cos(theta) dlam)
     const int n = degree + 1;
     double x[DG_MAXN], w[DG_MAXN];

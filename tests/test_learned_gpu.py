@@ -186,3 +186,9 @@ def test_pipeline_end_to_end_reports_plain_vs_learned(capsys):
     with capsys.disabled():
         print("\nlearned correction, 1 h, relative L2 (h, hu, hv): plain", ["%.2e" % v for v in ev["plain"]],
               "learned", ["%.2e" % v for v in ev["learned"]])
+    # what the network should gain: no field less accurate than plain coarse
+    # DG.  The reduced training here does not reach that; the loss is recorded
+    # as an expected failure (plain DG stays the default and the fallback)
+    # rather than hidden.
+    if not all(l <= p for l, p in zip(ev["learned"], ev["plain"])):
+        pytest.xfail("learned coarse solver less accurate than plain coarse DG after the reduced training")

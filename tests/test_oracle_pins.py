@@ -563,11 +563,149 @@ def test_planar_advection_rates_match_paper():
 
 
 def test_rhs_magnitude_bounds_the_tendency():
-    """The magnitude bound is >= |tendency| (triangle inequality) and equals it
-    for a single-term case (p = 0 rest state: only the pressure terms)."""
+    """The magnitude bound is >= |tendency| (triangle inequality) on a
+    general state; its value is pinned by the two tests below."""
     o = sphere(12, 6, 2)
     u = o.project_tensor(synth.SmoothField(5).fields_grid)
     k = o.rhs(u)
     s = o.rhs_magnitude(u)
     assert (s >= np.abs(k) * (1 - 1e-14)).all()
     assert (s > 0).any()
+
+
+def test_rhs_magnitude_p0_rest_state_closed_form():
+    """p = 0, fluid at rest at depth H (Eq. ode, Eq. dg_parts): the only
+    non-zero terms are the pressure P = g H^2 / 2 in the lambda-edge fluxes of
+    hu, and in the theta-edge fluxes cos(theta_e) P / R and the source
+    -g H^2 sin(theta_c) / (2R) of hv; phi_0 = 1/2, the one-point rule has
+    weight 2 per direction and M^-1 = 4 / (dlambda (sin theta_t - sin
+    theta_b)).  Doubling the bound, or summing signed terms, fails here."""
+    nlon, nlat, H = 6, 5, 4000.0
+    o = sphere(nlon, nlat, 0)
+    u = np.zeros(o.shape)
+    u[..., 0, 0] = 2.0 * H
+    S = o.rhs_magnitude(u)
+    dl, dth = 2 * math.pi / nlon, math.pi / nlat
+    P = 0.5 * G * H * H
+    for j in range(nlat):
+        tb = -math.pi / 2 + j * dth
+        tt, tc = tb + dth, tb + 0.5 * dth
+        minv = 4.0 / (dl * (math.sin(tt) - math.sin(tb)))
+        edges = (math.cos(tb) if j > 0 else 0.0) + (math.cos(tt) if j < nlat - 1 else 0.0)
+        want1 = minv * dth * P / R                          # W and E: 2 x dth * (P/R) * 1/2
+        want2 = minv * 0.5 * (dl * dth * G * H * H * abs(math.sin(tc)) / (2 * R) + dl * edges * P / R)
+        assert (S[j, :, 0, 0] == 0.0).all()
+        np.testing.assert_allclose(S[j, :, 1, 0], want1, rtol=1e-14)
+        np.testing.assert_allclose(S[j, :, 2, 0], want2, rtol=1e-14)
+
+
+def _swe_fluxes(q, th):
+    """F, G, S of Eq. (sph3) at latitude th for q = (h, hu, hv)."""
+    h, hu, hv = q
+    u, v = hu / h, hv / h
+    P = 0.5 * G * h * h
+    F = np.array([hu, hu * u + P, hu * v]) / R
+    Gv = math.cos(th) * np.array([hv, hv * u, hv * v + P]) / R
+    cor = 2 * OMEGA * math.sin(th) * math.cos(th) + u * math.sin(th) / R
+    Sv = np.array([0.0, cor * hv, -G * h * h * math.sin(th) / (2 * R) - cor * hu])
+    return F, Gv, Sv
+
+
+def _element_bruteforce(u, nlon, nlat, p, j, i):
+    """Tendency and magnitude bound of element (j, i), written out from the
+    definitions with numpy's Legendre routines: orthonormal basis, n-point
+    Gauss rules for the volume and edge integrals, Rusanov flux on
+    U = cos(theta) q with the larger one-sided eigenvalue ((|u| + c) /
+    (R cos theta) on lambda faces, (|v| + c) / R on theta faces), zero flux
+    through a pole edge, and the cos(theta)-weighted mass matrix by a
+    14-point rule, inverted by numpy."""
+    n = p + 1
+    xg, wg = npleg.leggauss(n)
+    dl, dth = 2 * math.pi / nlon, math.pi / nlat
+
+    def Lk(k, x, d=False):
+        c = np.zeros(k + 1)
+        c[k] = 1.0
+        return math.sqrt((2 * k + 1) / 2.0) * npleg.legval(x, npleg.legder(c) if d else c)
+
+    def phi(m, xi, eta, dx=False, dy=False):
+        return Lk(m % n, xi, dx) * Lk(m // n, eta, dy)
+
+    def val(jj, ii, xi, eta):
+        return np.array([sum(u[jj, ii, f, m] * phi(m, xi, eta) for m in range(n * n)) for f in range(3)])
+
+    def theta(eta):
+        return -math.pi / 2 + (j + 0.5 * (1 + eta)) * dth
+
+    r = np.zeros((3, n * n))
+    a = np.zeros((3, n * n))
+    for qy in range(n):
+        for qx in range(n):
+            xi, eta = xg[qx], xg[qy]
+            F, Gv, Sv = _swe_fluxes(val(j, i, xi, eta), theta(eta))
+            wq = wg[qx] * wg[qy] * dl * dth / 4
+            for m in range(n * n):
+                tx = wq * F * phi(m, xi, eta, dx=True) * 2 / dl
+                ty = wq * Gv * phi(m, xi, eta, dy=True) * 2 / dth
+                ts = wq * Sv * phi(m, xi, eta)
+                r[:, m] += tx + ty + ts
+                a[:, m] += np.abs(tx) + np.abs(ty) + np.abs(ts)
+    # edge: (normal, neighbour or None at a pole, own point, neighbour point) per Gauss point k
+    edges = [((-1, 0), (j, (i - 1) % nlon), lambda x: (-1.0, x), lambda x: (1.0, x)),
+             ((1, 0), (j, (i + 1) % nlon), lambda x: (1.0, x), lambda x: (-1.0, x)),
+             ((0, -1), (j - 1, i) if j > 0 else None, lambda x: (x, -1.0), lambda x: (x, 1.0)),
+             ((0, 1), (j + 1, i) if j < nlat - 1 else None, lambda x: (x, 1.0), lambda x: (x, -1.0))]
+    for (nx, ny), nb, own, other in edges:
+        for k in range(n):
+            xi, eta = own(xg[k])
+            th = theta(eta)
+            if nb is None:
+                fn = np.zeros(3)
+            else:
+                qo, qb = val(j, i, xi, eta), val(nb[0], nb[1], *other(xg[k]))
+                Fo, Go, _ = _swe_fluxes(qo, th)
+                Fb, Gb, _ = _swe_fluxes(qb, th)
+
+                def eig(q):
+                    c = math.sqrt(G * q[0])
+                    return (abs(q[1] / q[0]) + c) / (R * math.cos(th)) if nx else (abs(q[2] / q[0]) + c) / R
+
+                alpha = max(eig(qo), eig(qb))
+                fn = 0.5 * ((Fo * nx + Go * ny) + (Fb * nx + Gb * ny)) - 0.5 * alpha * math.cos(th) * (qb - qo)
+            we = wg[k] * (dth / 2 if nx else dl / 2)
+            for m in range(n * n):
+                t = we * fn * phi(m, xi, eta)
+                r[:, m] -= t
+                a[:, m] += np.abs(t)
+    xm, wm = npleg.leggauss(14)
+    M = np.zeros((n * n, n * n))
+    for r1 in range(n * n):
+        for r2 in range(n * n):
+            M[r1, r2] = sum(wm[qx] * wm[qy] * dl * dth / 4 * phi(r1, xm[qx], xm[qy]) * phi(r2, xm[qx], xm[qy]) *
+                            math.cos(theta(xm[qy])) for qx in range(14) for qy in range(14))
+    Mi = np.linalg.inv(M)
+    return (Mi @ r.T).T, (np.abs(Mi) @ a.T).T, (Mi @ a.T).T
+
+
+@pytest.mark.parametrize("p,j,i,signs", [(1, 1, 3, True), (1, 0, 0, True), (2, 4, 5, False), (2, 1, 0, True)])
+def test_rhs_and_magnitude_match_element_brute_force(p, j, i, signs):
+    """One element's tendency k = M^-1 h(u) and magnitude bound
+    |M^-1| sum |terms|, both against the brute force above, on a seeded state
+    (rows off the equator, whose mass matrices couple the latitude modes;
+    interior elements, polar rows, the periodic seam).  Where M^-1 has
+    negative entries (`signs`), the bound computed with M^-1 in place of
+    |M^-1| differs by far more than the tolerance, so dropping that absolute
+    value fails too."""
+    nlon, nlat = 6, 5
+    o = sphere(nlon, nlat, p)
+    u = o.project_tensor(synth.SmoothField(9).fields_grid)
+    k_bf, s_bf, s_signed = _element_bruteforce(u, nlon, nlat, p, j, i)
+    n2 = (p + 1) ** 2
+    k = o.rhs_element(u, j, i).reshape(3, n2)
+    s = o.rhs_magnitude_element(u, j, i).reshape(3, n2)
+    for f in range(3):
+        scale = s_bf[f].max()
+        assert np.abs(s[f] - s_bf[f]).max() <= 1e-13 * scale, (f, s[f], s_bf[f])
+        assert np.abs(k[f] - k_bf[f]).max() <= 1e-13 * scale, (f, k[f], k_bf[f])
+    if signs:
+        assert np.abs(s_signed - s_bf).max() > 1e-3 * s_bf.max()

@@ -1,14 +1,18 @@
 """Parity of the CUDA path (through the C-ABI) with the FP64 CPU oracle.
 
-Tolerances (per field, FP64 / FP32): 1e-12 / 1e-5.
+Tolerances, per field:
 * States (projection, time stepping): relative to the reference field,
-  ||x - y||_2 / ||y||_2 and max|x - y| / max|y|.
+  ||x - y||_2 / ||y||_2 and max|x - y| / max|y|, 1e-12 (FP64) / 1e-5 (FP32).
 * Tendencies (dg_rhs): relative to the oracle's magnitude bound
-  S = |M^-1| sum |terms|.  The tendency of this mesh is a small difference of
-  large terms (flux divergences of a nearly non-divergent flow, amplified by
-  1/cos(theta) in the polar rows), so any floating-point evaluation of it is
-  only determined up to a few units of roundoff times S; two correct FP64
-  evaluations differ by ~1e-10 relative to the tendency itself.
+  S = |M^-1| sum |terms| (pinned against a closed form and a brute force in
+  the oracle's own tests), 1e-14 (FP64) / 1e-6 (FP32), two orders of
+  magnitude above the errors the kernels show (~1e-16 / ~1e-8).  The
+  tendency of this mesh is a small difference of large terms (flux
+  divergences of a nearly non-divergent flow, amplified by 1/cos(theta) in
+  the polar rows), so any floating-point evaluation of it is only determined
+  up to a few units of roundoff times S.  The plain relative error
+  ||k - k_oracle||_2 / ||k_oracle||_2 of every tendency check is recorded
+  and printed at the end of the run.
 """
 import math
 import os
@@ -18,11 +22,13 @@ import pytest
 
 import oracle as O
 from paper_2303_11767_gb300 import dgswe, synth
+from _records import record_tendency
 
 pytestmark = pytest.mark.gpu
 
 R, G, OMEGA = synth.EARTH_RADIUS, 9.80616, 7.292e-5
 TOL = {"fp64": 1e-12, "fp32": 1e-5}
+TEND_TOL = {"fp64": 1e-14, "fp32": 1e-6}
 NTHREADS = os.cpu_count() or 1
 
 
@@ -53,8 +59,10 @@ def state_err(x, y):
     return out
 
 
-def tend_err(x, y, S):
+def tend_err(x, y, S, what=""):
     x = np.asarray(x).reshape(y.shape)
+    if what:
+        record_tendency(what, x, y, S)
     out = []
     for f in range(3):
         d = x[..., f, :] - y[..., f, :]
@@ -85,7 +93,8 @@ def test_rhs_parity_small_meshes(p, nlon, nlat, prec):
     o, u = case(nlon, nlat, p, 11)
     with solver(nlon, nlat, p, prec) as s:
         k = s.rhs(u)
-    assert_within(tend_err(k, o.rhs(u), o.rhs_magnitude(u)), TOL[prec], f"rhs p={p} {nlon}x{nlat} {prec}")
+    what = f"rhs p={p} {nlon}x{nlat} {prec}"
+    assert_within(tend_err(k, o.rhs(u), o.rhs_magnitude(u), what), TEND_TOL[prec], what)
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
@@ -94,7 +103,8 @@ def test_rhs_parity_configs(nlon, nlat, p, seed, prec):
     o, u = case(nlon, nlat, p, seed)
     with solver(nlon, nlat, p, prec) as s:
         k = s.rhs(u)
-    assert_within(tend_err(k, o.rhs(u), o.rhs_magnitude(u)), TOL[prec], f"rhs {nlon}x{nlat} p={p} {prec}")
+    what = f"rhs {nlon}x{nlat} p={p} {prec}"
+    assert_within(tend_err(k, o.rhs(u), o.rhs_magnitude(u), what), TEND_TOL[prec], what)
 
 
 # -------------------------------------------------------------- time steps --
@@ -169,7 +179,8 @@ def test_global_alpha_mode_matches_oracle(prec, tol):
         s.set_option(dgswe.OPT_ALPHA_MODE, 1)
         k = s.rhs(u)
         S = o.rhs_magnitude(u)
-        assert_within(tend_err(k, o.rhs(u), S), tol, f"global-alpha rhs {prec}")
+        assert_within(tend_err(k, o.rhs(u), S, f"global-alpha rhs {prec}"), TEND_TOL.get(prec, tol),
+                      f"global-alpha rhs {prec}")
         if prec == "fp64":   # the switch changes the tendency as it does in the oracle
             o_loc = oracle_sphere(nlon, nlat, p)
             d_or = o.rhs(u) - o_loc.rhs(u)
@@ -326,7 +337,7 @@ def test_rhs_parity_largest_mesh_sampled():
              (3, 29), (4, 30), (7, 31), (8, 32), (nlat // 2 + 1, 47), (nlat - 2, 1)}
     picks |= {(int(j), int(i)) for j, i in zip(rng.integers(0, nlat, 120), rng.integers(0, nlon, 120))}
     want = {(j, i): (o.rhs_element(u, j, i), o.rhs_magnitude_element(u, j, i)) for j, i in sorted(picks)}
-    for prec, tol in (("fp64", 1e-12), ("fp32", 1e-5), ("fp32_tc_bf16", 8 * 2.0 ** -9)):
+    for prec, tol in (("fp64", TEND_TOL["fp64"]), ("fp32", TEND_TOL["fp32"]), ("fp32_tc_bf16", 8 * 2.0 ** -9)):
         with solver(nlon, nlat, p, prec) as s:
             k = s.rhs(u)
         for (j, i), (kw, Sw) in want.items():
@@ -363,7 +374,8 @@ def test_well_balanced_option_matches_oracle(prec, tol):
         s.set_option(dgswe.OPT_WELL_BALANCED, 1)       # toggled with a resident state: kept
         assert_within(state_err(s.get_state(), u), 1e-7 if prec != "fp64" else 1e-15, "state kept")
         S = o.rhs_magnitude(u)
-        assert_within(tend_err(s.rhs(u), o.rhs(u), S), tol, f"well-balanced rhs {prec}")
+        assert_within(tend_err(s.rhs(u), o.rhs(u), S, f"well-balanced rhs {prec}"), TEND_TOL.get(prec, tol),
+                      f"well-balanced rhs {prec}")
         rest = np.zeros_like(u)
         rest[..., 0, 0] = 2.0 * 5000.0
         assert np.abs(s.rhs(rest)).max() == 0.0       # the rest state is exactly steady
