@@ -202,6 +202,66 @@ dg_status dg_get_time(dg_handle h, double *t);
 dg_status dg_set_time(dg_handle h, double t);
 
 /* ------------------------------------------------------------------------
+ * Latitude-band sharding of one mesh.  The paper (Sec. 5.1) names the
+ * Rusanov-flux phase as the only one that exchanges data between neighbouring
+ * elements: an element needs only its four neighbours' traces (Eq. rusanov),
+ * so contiguous latitude bands exchange one boundary row with each
+ * neighbouring band per Runge-Kutta stage.  A band
+ * handle owns rows [j_begin, j_end) of an nlon x nlat mesh; every state array
+ * of the handle also holds one ghost row below (j_begin > 0) and one above
+ * (j_end < nlat) the own rows, which receive the neighbour bands' rows.  Its
+ * state (dg_set_state, dg_get_state, dg_state_len) covers the own rows only,
+ * layout as above with j counted from j_begin.  The stage kernel is the
+ * whole mesh's, so a band split reproduces the whole mesh's stages bit for
+ * bit when every band uses the same reference depth
+ * (dg_band_set_reference_depth, FP32).  Supported: FP64 and FP32 stages, RK
+ * orders 1-4, the local Rusanov alpha, the well-balanced option.  dg_step,
+ * dg_rhs, dg_restrict_from, dg_attach_mlp, the tensor-core precisions and
+ * the global alpha mode return DG_EUNSUPPORTED on a band.  Per stage the
+ * driver packs each band's boundary rows, delivers them to the neighbours
+ * (any transport: a device copy, NCCL, host memory), unpacks them into the
+ * ghost rows, then calls dg_band_stage on every band.
+ * ------------------------------------------------------------------------ */
+
+/* Create the band [j_begin, j_end) of the nlon x nlat mesh of degree p
+ * (arguments otherwise as dg_create; 0 <= j_begin < j_end <= nlat). */
+dg_status dg_create_band(int nlon, int nlat, int j_begin, int j_end, int degree, double radius, double g,
+                         double omega, dg_handle *out);
+
+/* Values (of the working precision: double for FP64, float for FP32) of one
+ * halo message: a row's stage base followed by its stage increment,
+ * 2 * nlon * 3 * (p+1)^2.  0 for a handle that is not a band. */
+size_t dg_band_halo_len(dg_handle h);
+
+/* Reference depth of the FP32 storage (h is stored relative to it; FP64 only
+ * with the well-balanced option) for the next dg_set_state: give every band
+ * the whole mesh's mean element depth, 0.5 * sum_e u_e[h][0] / nel, so the
+ * bands hold the same bits as the whole mesh would. */
+dg_status dg_band_set_reference_depth(dg_handle h, double href);
+
+/* Copy the input of the next stage on own row 0 (side 0, south) or on the
+ * last own row (side 1, north) -- the row's u^n and the stage's increment
+ * (zeros for a stage without one) -- into d_out, a caller-owned device buffer
+ * of dg_band_halo_len values.  Ordered on the handle's stream. */
+dg_status dg_band_pack(dg_handle h, int side, void *d_out);
+
+/* Write a neighbour's packed row into the south (side 0) or north (side 1)
+ * ghost row, as the input of this band's next stage.  DG_EINVAL where that
+ * side is a pole.  Ordered on the handle's stream. */
+dg_status dg_band_unpack(dg_handle h, int side, const void *d_in);
+
+/* Run the next stage of the current time step (stage 1, 2, ... of the RK
+ * scheme of DG_OPT_RK_ORDER) with step size dt, which must stay the same
+ * within a step.  After a step's last stage the simulated time advances by
+ * dt and, with DG_OPT_CHECK_FINITE, the status is read as in dg_step. */
+dg_status dg_band_stage(dg_handle h, double dt);
+
+/* The band's mass as the compensated (Neumaier) pair of its fixed-order
+ * reduction: the band's mass is R^2 (sum + err); merging the bands' pairs in
+ * band order with an error-free two-sum gives the whole mesh's mass. */
+dg_status dg_band_mass_pair(dg_handle h, double *sum, double *err);
+
+/* ------------------------------------------------------------------------
  * Learned correction: a per-element multilayer perceptron (n_in -> H -> H ->
  * n_out, GELU (erf form), BF16 weights, FP32 accumulation, FP32 master
  * weights and Adam moments) trained on the GPU by the library's own forward

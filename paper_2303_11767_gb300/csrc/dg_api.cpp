@@ -108,6 +108,16 @@ struct dg_ctx {
     double plen = 1.0, fcor = 0; // planar domain side and f-plane Coriolis parameter
     int alpha_speed = 0;         // planar: Rusanov alpha = |beta| (1) or |beta . n| (0)
     BasisTab<double> pbasis{};   // planar: basis tables of degree p
+    // latitude band of a larger mesh (dg_create_band): the own rows are rows
+    // [j0, j0 + nlat) of a mesh of nlat_g rows; every state array holds, when
+    // gs / gn, one ghost row (a neighbour band's row) just before / after them
+    int band = 0, j0 = 0, nlat_g = 0, gs = 0, gn = 0;
+    size_t ghost_bytes = 0;    // byte offset of own row 0 in each state allocation
+    int band_stage = 0;        // the next stage of the current step
+    double band_dt = 0;        // step size of the current step
+    int href_fixed = 0;        // reference depth given by dg_band_set_reference_depth
+    double href_given = 0;
+    size_t row_len() const { return (size_t)nlon * 3 * nphi; }
     bool f32() const { return prec != DG_PREC_FP64; }                 // FP32 storage
     bool tc() const { return prec == DG_PREC_FP32_TC_BF16 || prec == DG_PREC_FP32_TC_FP16; }
 };
@@ -128,14 +138,18 @@ void free_state_buffers(dg_ctx *h)
     void **all[] = {&h->B[0], &h->B[1], &h->L[0], &h->L[1], &h->I[0], &h->I[1], &h->D,
                     &h->SB[0], &h->SB[1], &h->SL[0], &h->SL[1]};
     for (void **u : all) {
-        if (*u) cudaFree(*u);
+        if (*u) cudaFree(static_cast<char *>(*u) - h->ghost_bytes);
         *u = nullptr;
     }
 }
 
 dg_status alloc_state_buffers(dg_ctx *h)
 {
-    const size_t bytes = h->len * elem_size(h->prec);
+    // a band's arrays carry its ghost rows around the own rows; the pointers
+    // kept point at own row 0
+    const size_t es = elem_size(h->prec);
+    const size_t bytes = (h->len + (size_t)(h->gs + h->gn) * h->row_len()) * es;
+    h->ghost_bytes = (size_t)h->gs * h->row_len() * es;
     std::vector<void **> want = {&h->B[0], &h->B[1], &h->I[0], &h->I[1], &h->D};
     if (h->f32()) {
         want.push_back(&h->L[0]);
@@ -149,9 +163,17 @@ dg_status alloc_state_buffers(dg_ctx *h)
     }
     for (void **u : want) {
         if (cudaMalloc(u, bytes) != cudaSuccess) {
+            *u = nullptr;
             free_state_buffers(h);
             return fail(DG_ENOMEM, "cudaMalloc of %zu bytes failed", bytes);
         }
+        if (h->band && cudaMemset(*u, 0, bytes) != cudaSuccess) {   // ghost rows start at zero
+            cudaFree(*u);
+            *u = nullptr;
+            free_state_buffers(h);
+            return fail(DG_ECUDA, "cudaMemset failed");
+        }
+        *u = static_cast<char *>(*u) + h->ghost_bytes;
     }
     return DG_OK;
 }
@@ -166,6 +188,8 @@ StageArgs<T> base_args(dg_ctx *h, const RowTab<T> *rows, double href)
     a.status = h->d_status;
     a.nlon = h->nlon;
     a.nlat = h->nlat;
+    a.halo_s = h->gs;
+    a.halo_n = h->gn;
     a.href = (T)href;
     // the pressure of the rest state at href enters through the per-row
     // vector rho; the well-balanced option drops it (that state is steady)
@@ -257,13 +281,14 @@ dg_status enqueue_global_speeds(dg_ctx *h, StageArgs<T> &a)
     return DG_OK;
 }
 
+// Stage s of one RK step from u^n in base buffer `cur`.
 template <typename T>
-dg_status launch_step_t(dg_ctx *h, double dt, int cur, const RowTab<T> *rows)
+dg_status launch_stage_t(dg_ctx *h, double dt, int cur, const RowTab<T> *rows, int s)
 {
     StagePlan pl[4];
-    const int ns = rk_plan(h->rk, pl);
+    rk_plan(h->rk, pl);
     auto I = [&](int i) -> T * { return i < 0 ? nullptr : static_cast<T *>(h->I[i]); };
-    for (int s = 0; s < ns; ++s) {
+    {
         StageArgs<T> a = base_args<T>(h, rows, h->href);
         a.inc = I(pl[s].inc_in);
         a.inc_out = I(pl[s].inc_out);
@@ -305,6 +330,16 @@ dg_status launch_step_t(dg_ctx *h, double dt, int cur, const RowTab<T> *rows)
         if (r) return fail(DG_ECUDA, "stage kernel launch failed: %s", cudaGetErrorString(cudaGetLastError()));
         h->launches++;
     }
+    return DG_OK;
+}
+
+template <typename T>
+dg_status launch_step_t(dg_ctx *h, double dt, int cur, const RowTab<T> *rows)
+{
+    StagePlan pl[4];
+    const int ns = rk_plan(h->rk, pl);
+    for (int s = 0; s < ns; ++s)
+        if (dg_status st = launch_stage_t<T>(h, dt, cur, rows, s)) return st;
     return DG_OK;
 }
 
@@ -447,17 +482,31 @@ dg_status dg_set_device(int device)
     return DG_OK;
 }
 
-dg_status dg_create(int nlon, int nlat, int degree, double radius, double g, double omega, dg_handle *out)
+}  // extern "C"
+
+namespace {
+
+// A solver for rows [jb, je) of an nlon x nlat_g sphere mesh: the whole mesh
+// (dg_create) or one latitude band of it (dg_create_band).
+dg_status create_sphere(int nlon, int nlat_g, int jb, int je, int degree, double radius, double g, double omega,
+                        dg_handle *out)
 {
     if (!out) return fail(DG_EINVAL, "out is NULL");
     *out = nullptr;
-    if (nlon < 1 || nlat < 2) return fail(DG_EINVAL, "need nlon >= 1 and nlat >= 2 (got %d, %d)", nlon, nlat);
+    if (nlon < 1 || nlat_g < 2) return fail(DG_EINVAL, "need nlon >= 1 and nlat >= 2 (got %d, %d)", nlon, nlat_g);
+    if (jb < 0 || je > nlat_g || je <= jb) return fail(DG_EINVAL, "band rows [%d, %d) outside [0, %d)", jb, je, nlat_g);
     if (degree < 0 || degree > DG_MAXN - 1) return fail(DG_EINVAL, "degree must be in [0, %d]", DG_MAXN - 1);
     if (!(radius > 0) || !(g > 0) || !std::isfinite(omega))
         return fail(DG_EINVAL, "radius and g must be positive, omega finite");
-    if ((double)nlon * nlat > 2.0e9) return fail(DG_EINVAL, "mesh too large");
+    if ((double)nlon * nlat_g > 2.0e9) return fail(DG_EINVAL, "mesh too large");
     dg_ctx *h = new (std::nothrow) dg_ctx;
     if (!h) return fail(DG_ENOMEM, "host allocation failed");
+    const int nlat = je - jb;
+    h->band = (jb > 0 || je < nlat_g) ? 1 : 0;
+    h->j0 = jb;
+    h->nlat_g = nlat_g;
+    h->gs = jb > 0 ? 1 : 0;
+    h->gn = je < nlat_g ? 1 : 0;
     h->nlon = nlon;
     h->nlat = nlat;
     h->p = degree;
@@ -473,10 +522,15 @@ dg_status dg_create(int nlon, int nlat, int degree, double radius, double g, dou
         delete h;
         return fail(DG_ECUDA, "no CUDA device: %s", cudaGetErrorString(cudaGetLastError()));
     }
-    if (dg_build_tables(h->tab, nlon, nlat, degree, radius, g)) {
+    if (dg_build_tables(h->tab, nlon, nlat_g, degree, radius, g)) {
         dg_free_tables(h->tab);
         delete h;
         return fail(DG_EINVAL, "table construction failed");
+    }
+    if (h->band) {   // keep the own rows' tables (built for the whole mesh), first at index 0
+        std::memmove(h->tab.rows, h->tab.rows + jb, sizeof(RowTab<double>) * nlat);
+        std::memmove(h->tab.C, h->tab.C + (size_t)jb * h->nphi, sizeof(double) * (size_t)nlat * h->nphi);
+        h->tab.nlat = nlat;
     }
 #define CREATE_TRY(x)                 \
     do {                              \
@@ -503,7 +557,7 @@ dg_status dg_create(int nlon, int nlat, int degree, double radius, double g, dou
         std::vector<double> c0((size_t)nlat * h->n + nlat);
         for (int j = 0; j < nlat; ++j) {
             for (int b = 0; b < h->n; ++b) c0[(size_t)j * h->n + b] = h->tab.C[(size_t)j * h->nphi + b];
-            const double tb = -0.5 * M_PI + j * h->tab.dth;
+            const double tb = -0.5 * M_PI + (h->j0 + j) * h->tab.dth;
             c0[(size_t)nlat * h->n + j] = std::sin(tb + h->tab.dth) - std::sin(tb);
         }
         if (cudaMalloc(&h->c0, c0.size() * sizeof(double)) != cudaSuccess) {
@@ -516,7 +570,7 @@ dg_status dg_create(int nlon, int nlat, int degree, double radius, double g, dou
         }
     }
     h->nblocks = dg_mass_blocks(h->nel);
-    if (cudaMalloc(&h->partials, 2 * sizeof(double) * h->nblocks) != cudaSuccess ||
+    if (cudaMalloc(&h->partials, 2 * sizeof(double) * (h->nblocks + 1)) != cudaSuccess ||   // + the pair
         cudaMalloc(&h->d_result, sizeof(double)) != cudaSuccess ||
         cudaMalloc(&h->d_status, sizeof(unsigned)) != cudaSuccess ||
         cudaMalloc(&h->d_maxbits, sizeof(unsigned long long)) != cudaSuccess ||
@@ -531,6 +585,21 @@ dg_status dg_create(int nlon, int nlat, int degree, double radius, double g, dou
 #undef CREATE_TRY
     *out = h;
     return DG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+dg_status dg_create(int nlon, int nlat, int degree, double radius, double g, double omega, dg_handle *out)
+{
+    return create_sphere(nlon, nlat, 0, nlat, degree, radius, g, omega, out);
+}
+
+dg_status dg_create_band(int nlon, int nlat, int j_begin, int j_end, int degree, double radius, double g,
+                         double omega, dg_handle *out)
+{
+    return create_sphere(nlon, nlat, j_begin, j_end, degree, radius, g, omega, out);
 }
 
 dg_status dg_create_plane_swe(int nx, int ny, int degree, double L, double g, double f, dg_handle *out)
@@ -654,6 +723,9 @@ dg_status dg_set_option(dg_handle h, int key, long long value)
         return planar_unsupported(h, key == DG_OPT_PRECISION ? "a precision other than FP64"
                                      : key == DG_OPT_ALPHA_MODE ? "the global alpha mode"
                                                                 : "the well-balanced option");
+    if (h->band && ((key == DG_OPT_PRECISION && (value == DG_PREC_FP32_TC_BF16 || value == DG_PREC_FP32_TC_FP16)) ||
+                    (key == DG_OPT_ALPHA_MODE && value)))
+        return fail(DG_EUNSUPPORTED, "a latitude band supports the FP64 and FP32 stages with the local Rusanov alpha");
     switch (key) {
     case DG_OPT_PRECISION: {
         if (value < DG_PREC_FP64 || value > DG_PREC_FP32_TC_FP16) return fail(DG_EINVAL, "unknown precision %lld", value);
@@ -681,7 +753,7 @@ dg_status dg_set_option(dg_handle h, int key, long long value)
                                       sizeof(double), h->nel, cudaMemcpyDeviceToHost));
                 double s = 0;
                 for (double v : m0) s += v;
-                h->href = 0.5 * s / (double)h->nel;
+                h->href = h->href_fixed ? h->href_given : 0.5 * s / (double)h->nel;
             } else {
                 h->href = 0.0;
             }
@@ -708,7 +780,7 @@ dg_status dg_set_option(dg_handle h, int key, long long value)
                                       sizeof(double), h->nel, cudaMemcpyDeviceToHost));
                 double sum = 0;
                 for (double v : m0) sum += v;
-                h->href = 0.5 * sum / (double)h->nel;
+                h->href = h->href_fixed ? h->href_given : 0.5 * sum / (double)h->nel;
             }
             h->cur = 0;
             if (dg_status s = to_internal(h, h->stage64, h->B[0], h->L[0], h->href)) return s;
@@ -766,7 +838,7 @@ dg_status dg_set_state_device(dg_handle h, const double *d_modal, size_t len)
         CUDA_TRY(cudaStreamSynchronize(h->stream));
         double s = 0;
         for (double v : m0) s += v;
-        h->href = 0.5 * s / (double)h->nel;
+        h->href = h->href_fixed ? h->href_given : 0.5 * s / (double)h->nel;
     }
     h->cur = 0;
     if (dg_status s = to_internal(h, h->stage64, h->B[0], h->L[0], h->href)) return s;
@@ -788,7 +860,7 @@ dg_status dg_set_state(dg_handle h, const double *modal, size_t len)
         return DG_OK;
     }
     CUDA_TRY(cudaMemcpyAsync(h->stage64, modal, len * sizeof(double), cudaMemcpyHostToDevice, h->stream));
-    h->href = (h->f32() || h->wb) ? mean_depth(modal, h->nel, h->nphi) : 0.0;
+    h->href = (h->f32() || h->wb) ? (h->href_fixed ? h->href_given : mean_depth(modal, h->nel, h->nphi)) : 0.0;
     h->cur = 0;
     if (dg_status s = to_internal(h, h->stage64, h->B[0], h->L[0], h->href)) return s;
     CUDA_TRY(cudaStreamSynchronize(h->stream));   // the host buffer is only borrowed
@@ -830,6 +902,7 @@ dg_status dg_rhs(dg_handle h, const double *modal_in, double *tend_out, size_t l
 {
     if (dg_status s = check(h)) return s;
     if (!modal_in || !tend_out || len != h->len) return fail(DG_EINVAL, "state length %zu, expected %zu", len, h->len);
+    if (h->band) return fail(DG_EUNSUPPORTED, "dg_rhs needs a whole mesh (a band's ghost rows are not inputs)");
     DeviceGuard dg(h->device);
     // scratch: the increment buffers are free between steps
     void *in = h->I[0], *outb = h->I[1];
@@ -901,6 +974,9 @@ dg_status dg_step(dg_handle h, int n, double dt)
     if (n < 0) return fail(DG_EINVAL, "n must be >= 0");
     if (!(dt > 0) || !std::isfinite(dt)) return fail(DG_EINVAL, "dt must be positive and finite");
     if (!h->have_state) return fail(DG_EINVAL, "no state set");
+    if (h->band)
+        return fail(DG_EUNSUPPORTED, "a latitude band advances one stage at a time (dg_band_stage), after its "
+                                     "ghost rows have received the neighbours' rows");
     if (n == 0) return DG_OK;
     DeviceGuard dg(h->device);
     if (h->tc())
@@ -968,17 +1044,17 @@ dg_status dg_step(dg_handle h, int n, double dt)
 }  // extern "C"
 
 namespace {
-dg_status enqueue_mass(dg_ctx *h, double *d_out)
+dg_status enqueue_mass(dg_ctx *h, double *d_out, double *d_pair = nullptr)
 {
     int r = h->prec == DG_PREC_FP64
                 ? dg_launch_mass<double>(static_cast<const double *>(h->B[h->cur]),
                                          static_cast<const double *>(h->L[h->cur]), h->c0, h->nlon, h->nlat, h->n,
                                          h->href, h->tab.dlam, h->tab.dth, h->R * h->R, h->partials, h->nblocks,
-                                         d_out, h->stream)
+                                         d_out, d_pair, h->stream)
                 : dg_launch_mass<float>(static_cast<const float *>(h->B[h->cur]),
                                         static_cast<const float *>(h->L[h->cur]), h->c0, h->nlon, h->nlat, h->n,
                                         h->href, h->tab.dlam, h->tab.dth, h->R * h->R, h->partials, h->nblocks,
-                                        d_out, h->stream);
+                                        d_out, d_pair, h->stream);
     if (r) return fail(DG_ECUDA, "mass kernel failed: %s", cudaGetErrorString(cudaGetLastError()));
     h->aux_launches += 2;
     return DG_OK;
@@ -1079,7 +1155,7 @@ dg_status dg_projection_nodes(dg_handle h, double *lam, size_t nlam, double *the
         for (int q = 0; q < nm; ++q) lam[(size_t)i * nm + q] = (i + 0.5 * (1.0 + h->tab.xm[q])) * h->tab.dlam;
     for (int j = 0; j < h->nlat; ++j)
         for (int q = 0; q < nm; ++q)
-            theta[(size_t)j * nm + q] = -0.5 * M_PI + (j + 0.5 * (1.0 + h->tab.xm[q])) * h->tab.dth;
+            theta[(size_t)j * nm + q] = -0.5 * M_PI + (h->j0 + j + 0.5 * (1.0 + h->tab.xm[q])) * h->tab.dth;
     return DG_OK;
 }
 
@@ -1120,7 +1196,7 @@ dg_status dg_project_nodal(dg_handle h, const double *nodal, size_t len_nodal, d
     for (int a = 0; a < n; ++a)
         for (int q = 0; q < nm; ++q) PL[(size_t)a * nm + q] = h->tab.wm[q] * dg_legendre(a, h->tab.xm[q]);
     for (int j = 0; j < h->nlat; ++j) {
-        const double tb = -0.5 * M_PI + j * h->tab.dth;
+        const double tb = -0.5 * M_PI + (h->j0 + j) * h->tab.dth;
         for (int b = 0; b < n; ++b)
             for (int q = 0; q < nm; ++q)
                 PC[(size_t)b * nm + q] =
@@ -1157,6 +1233,7 @@ dg_status dg_project_nodal(dg_handle h, const double *nodal, size_t len_nodal, d
 dg_status dg_attach_mlp(dg_handle h, dg_mlp m)
 {
     if (dg_status s = check(h)) return s;
+    if (h->band && m) return fail(DG_EUNSUPPORTED, "the learned source needs a whole mesh");
     DeviceGuard dg(h->device);
     CUDA_TRY(cudaStreamSynchronize(h->stream));
     drop_graphs(h);
@@ -1178,6 +1255,7 @@ dg_status dg_restrict_from(dg_handle coarse, dg_handle fine)
     if (dg_status s = check(coarse)) return s;
     if (dg_status s = check(fine)) return s;
     if (coarse->physics != 0 || fine->physics != 0) return planar_unsupported(coarse, "dg_restrict_from");
+    if (coarse->band || fine->band) return fail(DG_EUNSUPPORTED, "dg_restrict_from needs whole meshes");
     if (!fine->have_state) return fail(DG_EINVAL, "the fine solver has no state");
     if (coarse->device != fine->device) return fail(DG_EINVAL, "the solvers live on different devices");
     const int r = fine->nlon / coarse->nlon;
@@ -1234,6 +1312,113 @@ dg_status dg_measure_fp64_peak(int reps, double *gflops)
     if (!gflops || reps < 1) return fail(DG_EINVAL, "need reps >= 1 and gflops");
     if (dg_probe_fp64_gflops(reps, gflops))
         return fail(DG_ECUDA, "FP64 probe failed: %s", cudaGetErrorString(cudaGetLastError()));
+    return DG_OK;
+}
+
+// ------------------------------------------------------ latitude bands --
+
+size_t dg_band_halo_len(dg_handle h) { return h && h->band ? 2 * h->row_len() : 0; }
+
+dg_status dg_band_set_reference_depth(dg_handle h, double href)
+{
+    if (dg_status s = check(h)) return s;
+    if (!h->band) return fail(DG_EINVAL, "not a band handle");
+    if (!(href > 0) || !std::isfinite(href)) return fail(DG_EINVAL, "the reference depth must be positive");
+    h->href_fixed = 1;
+    h->href_given = href;
+    return DG_OK;
+}
+
+namespace {
+// The current stage's input: u^n in B[cur] and the increment the stage reads
+// (null for a stage without one).
+void band_stage_inputs(dg_ctx *h, char **base, char **inc)
+{
+    StagePlan pl[4];
+    rk_plan(h->rk, pl);
+    const int ii = pl[h->band_stage].inc_in;
+    *base = static_cast<char *>(h->B[h->cur]);
+    *inc = ii >= 0 ? static_cast<char *>(h->I[ii]) : nullptr;
+}
+}  // namespace
+
+dg_status dg_band_pack(dg_handle h, int side, void *d_out)
+{
+    if (dg_status s = check(h)) return s;
+    if (!h->band) return fail(DG_EINVAL, "not a band handle");
+    if (!d_out || (side != 0 && side != 1)) return fail(DG_EINVAL, "need side 0 (south) or 1 (north) and d_out");
+    if (!h->have_state) return fail(DG_EINVAL, "no state set");
+    DeviceGuard dg(h->device);
+    const size_t rb = h->row_len() * elem_size(h->prec);
+    char *base, *inc;
+    band_stage_inputs(h, &base, &inc);
+    const size_t off = side == 0 ? 0 : (size_t)(h->nlat - 1) * rb;
+    char *o = static_cast<char *>(d_out);
+    CUDA_TRY(cudaMemcpyAsync(o, base + off, rb, cudaMemcpyDeviceToDevice, h->stream));
+    if (inc) CUDA_TRY(cudaMemcpyAsync(o + rb, inc + off, rb, cudaMemcpyDeviceToDevice, h->stream));
+    else CUDA_TRY(cudaMemsetAsync(o + rb, 0, rb, h->stream));
+    return DG_OK;
+}
+
+dg_status dg_band_unpack(dg_handle h, int side, const void *d_in)
+{
+    if (dg_status s = check(h)) return s;
+    if (!h->band) return fail(DG_EINVAL, "not a band handle");
+    if (!d_in || (side != 0 && side != 1)) return fail(DG_EINVAL, "need side 0 (south) or 1 (north) and d_in");
+    if ((side == 0 && !h->gs) || (side == 1 && !h->gn)) return fail(DG_EINVAL, "no ghost row on that side (a pole)");
+    if (!h->have_state) return fail(DG_EINVAL, "no state set");
+    DeviceGuard dg(h->device);
+    const size_t rb = h->row_len() * elem_size(h->prec);
+    char *base, *inc;
+    band_stage_inputs(h, &base, &inc);
+    // the south ghost row sits just before own row 0, the north one just after the last own row
+    const ptrdiff_t off = side == 0 ? -(ptrdiff_t)rb : (ptrdiff_t)h->nlat * (ptrdiff_t)rb;
+    const char *in = static_cast<const char *>(d_in);
+    CUDA_TRY(cudaMemcpyAsync(base + off, in, rb, cudaMemcpyDeviceToDevice, h->stream));
+    if (inc) CUDA_TRY(cudaMemcpyAsync(inc + off, in + rb, rb, cudaMemcpyDeviceToDevice, h->stream));
+    return DG_OK;
+}
+
+dg_status dg_band_stage(dg_handle h, double dt)
+{
+    if (dg_status s = check(h)) return s;
+    if (!h->band) return fail(DG_EINVAL, "not a band handle");
+    if (!(dt > 0) || !std::isfinite(dt)) return fail(DG_EINVAL, "dt must be positive and finite");
+    if (!h->have_state) return fail(DG_EINVAL, "no state set");
+    StagePlan pl[4];
+    const int ns = rk_plan(h->rk, pl);
+    if (h->band_stage >= ns) h->band_stage = 0;   // the RK order changed between steps
+    if (h->band_stage == 0) h->band_dt = dt;
+    else if (dt != h->band_dt) return fail(DG_EINVAL, "dt changed within a step");
+    DeviceGuard dg(h->device);
+    const int s = h->band_stage;
+    dg_status st = h->prec == DG_PREC_FP64 ? launch_stage_t<double>(h, dt, h->cur, h->rows64, s)
+                                           : launch_stage_t<float>(h, dt, h->cur, h->rows32, s);
+    if (st) return st;
+    if (pl[s].fin) {
+        h->cur ^= 1;
+        h->band_stage = 0;
+        h->t += dt;
+        if (h->check) return read_status(h);
+    } else {
+        h->band_stage = s + 1;
+    }
+    return DG_OK;
+}
+
+dg_status dg_band_mass_pair(dg_handle h, double *sum, double *err)
+{
+    if (dg_status s = check(h)) return s;
+    if (h->physics != 0) return planar_unsupported(h, "dg_band_mass_pair");
+    if (!sum || !err) return fail(DG_EINVAL, "sum and err must not be NULL");
+    if (!h->have_state) return fail(DG_EINVAL, "no state set");
+    DeviceGuard dg(h->device);
+    if (dg_status s = enqueue_mass(h, nullptr, h->partials + 2 * h->nblocks)) return s;
+    double pair[2];
+    CUDA_TRY(cudaMemcpyAsync(pair, h->partials + 2 * h->nblocks, sizeof pair, cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
+    *sum = pair[0];
+    *err = pair[1];
     return DG_OK;
 }
 

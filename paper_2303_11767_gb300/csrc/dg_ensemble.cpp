@@ -493,7 +493,7 @@ dg_status dg_ensemble_total_mass(dg_ensemble e, int member, double *mass)
     const HostTables &t = e->tabs[member];
     if (dg_launch_mass<float>(e->B[e->cur] + e->off[member], e->L[e->cur] + e->off[member], e->c0 + e->c0_off[member],
                               e->nlon[member], e->nlat[member], n, e->href[member], t.dlam, t.dth, e->R * e->R,
-                              e->partials, e->nblocks, e->d_result, e->stream))
+                              e->partials, e->nblocks, e->d_result, nullptr, e->stream))
         return efail(DG_ECUDA, "mass kernel failed");
     ECUDA(cudaMemcpyAsync(mass, e->d_result, sizeof(double), cudaMemcpyDeviceToHost, e->stream));
     ECUDA(cudaStreamSynchronize(e->stream));

@@ -87,6 +87,10 @@ struct StageArgs {
     const RowTab<T> *rows;
     unsigned int *status;
     int nlon, nlat;
+    // latitude-band sharding: 1 when the row south of row 0 (halo_s) or north
+    // of row nlat - 1 (halo_n) is a neighbour band's row, held in the state
+    // arrays just before / after the band's own rows, instead of a pole
+    int halo_s, halo_n;
     T href;          // reference depth: h = href + stored h
     T P0;            // g href^2 / 2 (pressure carried by the rho table)
     T g, cF, cG, invR, twoOmega;
@@ -159,10 +163,12 @@ template <typename T>
 int dg_launch_to_internal(const double *src, T *dst, T *lo, size_t nel, int nphi, double href, void *stream);
 template <typename T>
 int dg_launch_to_api(const T *src, const T *lo, double *dst, size_t nel, int nphi, double href, void *stream);
+// result (may be null): scale * (sum + correction); pair (may be null): the
+// unscaled compensated pair (sum, correction) itself.
 template <typename T>
 int dg_launch_mass(const T *u, const T *lo, const double *c0, int nlon, int nlat, int n, double href,
                    double dlam, double dth, double scale, double *partials, int nblocks, double *result,
-                   void *stream);
+                   double *pair, void *stream);
 // Global Rusanov speeds of the stage state base + inc (inc may be null): the
 // maxima of |u| + sqrt(g h) and |v| + sqrt(g h) over all Gauss points, as the
 // bits of T atomically maxed into out[0], out[1] (zero them first).  lanes:

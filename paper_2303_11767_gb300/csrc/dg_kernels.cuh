@@ -306,7 +306,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &A, int bx, int by
     //      (W / E columns, S / N rows; periodic in lambda, none across a pole),
     //      copied asynchronously by all threads, the base to ef[0, HALO_CAP)
     //      and the increment to ef[HALO_CAP, 2 HALO_CAP)
-    const bool hasS = j0 > 0, hasN = j0 + Wv < A.nlat;
+    const bool hasS = j0 > 0 || A.halo_s, hasN = j0 + Wv < A.nlat || A.halo_n;
     const int nSe = hasS ? Gv : 0, nNe = hasN ? Gv : 0;
     {
         constexpr int VPC = SM::CP / (int)sizeof(T), CPE = EL / VPC;
@@ -330,7 +330,8 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &A, int bx, int by
                 hj = north ? j0 + Wv : j0 - 1;
                 hi = i0 + (north ? r - nSe : r);
             }
-            const size_t o = ((size_t)hj * A.nlon + hi) * EL + c;
+            // hj = -1 is a neighbour band's row held just before row 0
+            const long long o = ((long long)hj * A.nlon + hi) * EL + c;
             cp_async<SM::CP>(ef + h * EL + c, A.base + o);
             if (has_inc) cp_async<SM::CP>(ef + GE::HALO_CAP + h * EL + c, incp + o);
         }
@@ -484,7 +485,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &A, int bx, int by
             rusanov_lam(nb, tr[0], href, gg, A.cF, fx, st, ga_l);
 #pragma unroll
             for (int f = 0; f < 3; ++f) ef[(own * 2 + 0) * 3 * N + f * N + k] = fx[f];
-            if (j > 0) {
+            if (j > 0 || A.halo_s) {
                 const T *tS = trc + (own - TW) * TRC;
 #pragma unroll
                 for (int f = 0; f < 3; ++f) nb[f] = tS[(3 * 3 + f) * N + k];   // S neighbour's N trace
@@ -496,7 +497,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &A, int bx, int by
 #pragma unroll
             for (int f = 0; f < 3; ++f) ef[(own * 2 + 1) * 3 * N + f * N + k] = fx[f];
         }
-        const int nE = Wv * N, nN = (j0 + Wv < A.nlat) ? Gv * N : 0;
+        const int nE = Wv * N, nN = hasN ? Gv * N : 0;
         const int it = 32 * W - 1 - tid;   // the last warps, which have no halo items
         if (it < nE + nN) {
             T L[3], R[3];
@@ -535,7 +536,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &A, int bx, int by
 #pragma unroll
         for (int f = 0; f < 3; ++f) {
             GsS[f] = ef[(own * 2 + 1) * 3 * N + f * N + k];
-            GsN[f] = (valid && j < A.nlat - 1) ? ef[((own + TW) * 2 + 1) * 3 * N + f * N + k] : T(0);
+            GsN[f] = (valid && (j < A.nlat - 1 || A.halo_n)) ? ef[((own + TW) * 2 + 1) * 3 * N + f * N + k] : T(0);
         }
         T X1[3][N], X2[3][N];
 #pragma unroll
@@ -819,6 +820,7 @@ __global__ void __launch_bounds__(32 * W, 24 / W) ensemble_kernel(const EnsArgs<
         A.status = E.status;
         A.nlon = m.nlon;
         A.nlat = m.nlat;
+        A.halo_s = A.halo_n = 0;
         A.href = m.href;
         A.P0 = m.P0;
         A.g = E.g;
@@ -963,7 +965,8 @@ __global__ void __launch_bounds__(MASS_THREADS) mass_partial_kernel(const T *__r
 }
 
 static __global__ void __launch_bounds__(MASS_THREADS) mass_final_kernel(const double *__restrict__ partials, int nblocks,
-                                                                  double scale, double *__restrict__ result)
+                                                                  double scale, double *__restrict__ result,
+                                                                  double *__restrict__ pair)
 {
     __shared__ CSum red[MASS_THREADS];
     CSum acc{0.0, 0.0};
@@ -975,7 +978,13 @@ static __global__ void __launch_bounds__(MASS_THREADS) mass_final_kernel(const d
         if (threadIdx.x < s) red[threadIdx.x] = csum_merge(red[threadIdx.x], red[threadIdx.x + s]);
         __syncthreads();
     }
-    if (threadIdx.x == 0) *result = scale * (red[0].s + red[0].c);
+    if (threadIdx.x == 0) {
+        if (result) *result = scale * (red[0].s + red[0].c);
+        if (pair) {
+            pair[0] = red[0].s;
+            pair[1] = red[0].c;
+        }
+    }
 }
 
 // Largest sqrt(u^2 + v^2) + sqrt(g h) over the n x n Gauss points; one thread
@@ -1175,14 +1184,14 @@ int dg_launch_to_api<DG_REAL>(const DG_REAL *src, const DG_REAL *lo, double *dst
 template <>
 int dg_launch_mass<DG_REAL>(const DG_REAL *u, const DG_REAL *lo, const double *c0, int nlon, int nlat, int n,
                             double href, double dlam, double dth, double scale, double *partials, int nblocks,
-                            double *result, void *stream)
+                            double *result, double *pair, void *stream)
 {
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const size_t nel = (size_t)nlon * nlat;
     const size_t chunk = (nel + nblocks - 1) / nblocks;
     dgk::mass_partial_kernel<DG_REAL><<<nblocks, dgk::MASS_THREADS, 0, s>>>(u, lo, c0, nlon, nlat, n, href,
                                                                             0.5 * dlam * dth, dlam, chunk, partials);
-    dgk::mass_final_kernel<<<1, dgk::MASS_THREADS, 0, s>>>(partials, nblocks, scale, result);
+    dgk::mass_final_kernel<<<1, dgk::MASS_THREADS, 0, s>>>(partials, nblocks, scale, result, pair);
     return cudaPeekAtLastError() == cudaSuccess ? 0 : 1;
 }
 

@@ -91,6 +91,15 @@ SIGNATURES = {
     "dg_ensemble_autotune": (ctypes.c_int, [_H, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                             ctypes.POINTER(ctypes.c_int), _dp]),
     "dg_ensemble_stage_launches": (ctypes.c_longlong, [_H]),
+    "dg_create_band": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                      ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                      ctypes.POINTER(ctypes.c_void_p)]),
+    "dg_band_halo_len": (ctypes.c_size_t, [_H]),
+    "dg_band_set_reference_depth": (ctypes.c_int, [_H, ctypes.c_double]),
+    "dg_band_pack": (ctypes.c_int, [_H, ctypes.c_int, ctypes.c_void_p]),
+    "dg_band_unpack": (ctypes.c_int, [_H, ctypes.c_int, ctypes.c_void_p]),
+    "dg_band_stage": (ctypes.c_int, [_H, ctypes.c_double]),
+    "dg_band_mass_pair": (ctypes.c_int, [_H, _dp, _dp]),
 }
 
 _lib = None
@@ -176,6 +185,57 @@ class Solver:
         self.set_option(OPT_PRECISION, PREC[precision] if isinstance(precision, str) else int(precision))
         self.set_option(OPT_RK_ORDER, rk_order)
         self.set_option(OPT_CHECK_FINITE, int(bool(check_finite)))
+
+    @classmethod
+    def band(cls, nlon, nlat, j_begin, j_end, degree, radius=EARTH_RADIUS, g=GRAVITY, omega=OMEGA,
+             precision="fp64", rk_order=3, check_finite=True):
+        """Rows [j_begin, j_end) of the nlon x nlat mesh (dg_create_band);
+        state shape (j_end - j_begin, nlon, 3, (p+1)^2)."""
+        self = cls.__new__(cls)
+        h = ctypes.c_void_p()
+        _check(lib().dg_create_band(int(nlon), int(nlat), int(j_begin), int(j_end), int(degree), float(radius),
+                                    float(g), float(omega), ctypes.byref(h)))
+        self._h = h
+        self.nlon, self.nlat, self.degree = int(nlon), int(j_end) - int(j_begin), int(degree)
+        self.j_begin, self.j_end, self.nlat_global = int(j_begin), int(j_end), int(nlat)
+        self.n = self.degree + 1
+        self.nphi = self.n * self.n
+        self.nm = self.degree + 9
+        self.radius, self.g, self.omega = float(radius), float(g), float(omega)
+        self.nfields = 3
+        self.set_option(OPT_PRECISION, PREC[precision] if isinstance(precision, str) else int(precision))
+        self.set_option(OPT_RK_ORDER, rk_order)
+        self.set_option(OPT_CHECK_FINITE, int(bool(check_finite)))
+        return self
+
+    @property
+    def halo_len(self):
+        """Values of one halo message (dg_band_halo_len)."""
+        return int(lib().dg_band_halo_len(self._h))
+
+    def set_reference_depth(self, href):
+        _check(lib().dg_band_set_reference_depth(self._h, float(href)), self._h)
+
+    def pack(self, side, t):
+        """Boundary row (side 0 south, 1 north) of the next stage's input into
+        the contiguous device tensor t (halo_len values of the working type)."""
+        assert t.is_contiguous() and t.numel() == self.halo_len
+        _check(lib().dg_band_pack(self._h, int(side), ctypes.c_void_p(t.data_ptr())), self._h)
+
+    def unpack(self, side, t):
+        """A neighbour's packed row into the south (0) / north (1) ghost row."""
+        assert t.is_contiguous() and t.numel() == self.halo_len
+        _check(lib().dg_band_unpack(self._h, int(side), ctypes.c_void_p(t.data_ptr())), self._h)
+
+    def stage(self, dt):
+        """The next RK stage of the current step (dg_band_stage)."""
+        _check(lib().dg_band_stage(self._h, float(dt)), self._h)
+
+    def mass_pair(self):
+        """(sum, err): the band's mass is radius^2 (sum + err)."""
+        a, b = ctypes.c_double(), ctypes.c_double()
+        _check(lib().dg_band_mass_pair(self._h, ctypes.byref(a), ctypes.byref(b)), self._h)
+        return a.value, b.value
 
     @classmethod
     def plane_advection(cls, nx, ny, degree, bx=1.0, by=1.0, alpha_speed=False, rk_order=4, check_finite=True):

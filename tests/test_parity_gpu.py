@@ -5,8 +5,12 @@ Tolerances, per field:
   ||x - y||_2 / ||y||_2 and max|x - y| / max|y|, 1e-12 (FP64) / 1e-5 (FP32).
 * Tendencies (dg_rhs): relative to the oracle's magnitude bound
   S = |M^-1| sum |terms| (pinned against a closed form and a brute force in
-  the oracle's own tests), 1e-14 (FP64) / 1e-6 (FP32), two orders of
-  magnitude above the errors the kernels show (~1e-16 / ~1e-8).  The
+  the oracle's own tests).  FP64: 3e-14, twice the summation bound
+  gamma_N = N u / (1 - N u) (u = 2^-53) with N ~ 3 n^2 + 5 n ~ 100 terms per
+  tendency entry at degree 4, once for each of the two evaluations compared;
+  the observed errors are ~1e-16 over a whole mesh and up to 1.1e-14 for
+  single elements.  FP32: 1e-6, below that bound (1.2e-5) and ~20x above the
+  observed ~5e-8.  The
   tendency of this mesh is a small difference of large terms (flux
   divergences of a nearly non-divergent flow, amplified by 1/cos(theta) in
   the polar rows), so any floating-point evaluation of it is only determined
@@ -28,7 +32,7 @@ pytestmark = pytest.mark.gpu
 
 R, G, OMEGA = synth.EARTH_RADIUS, 9.80616, 7.292e-5
 TOL = {"fp64": 1e-12, "fp32": 1e-5}
-TEND_TOL = {"fp64": 1e-14, "fp32": 1e-6}
+TEND_TOL = {"fp64": 3e-14, "fp32": 1e-6}
 NTHREADS = os.cpu_count() or 1
 
 
@@ -337,7 +341,10 @@ def test_rhs_parity_largest_mesh_sampled():
              (3, 29), (4, 30), (7, 31), (8, 32), (nlat // 2 + 1, 47), (nlat - 2, 1)}
     picks |= {(int(j), int(i)) for j, i in zip(rng.integers(0, nlat, 120), rng.integers(0, nlon, 120))}
     want = {(j, i): (o.rhs_element(u, j, i), o.rhs_magnitude_element(u, j, i)) for j, i in sorted(picks)}
-    for prec, tol in (("fp64", TEND_TOL["fp64"]), ("fp32", TEND_TOL["fp32"]), ("fp32_tc_bf16", 8 * 2.0 ** -9)):
+    # per element, relative to its own bound: FP64 3e-14 as everywhere; FP32
+    # 1e-5, the summation bound 2 gamma_N of FP32 (the whole-mesh 1e-6 is
+    # taken against the mesh's largest bound)
+    for prec, tol in (("fp64", TEND_TOL["fp64"]), ("fp32", 1e-5), ("fp32_tc_bf16", 8 * 2.0 ** -9)):
         with solver(nlon, nlat, p, prec) as s:
             k = s.rhs(u)
         for (j, i), (kw, Sw) in want.items():
