@@ -57,9 +57,13 @@ CFL = 0.1
 FLUSH_BYTES = 256 << 20
 # precision -> arithmetic of the path ("+bf16tc": FP32 stage arithmetic with the
 # basis contractions on BF16 tensor cores, FP32 accumulation)
-DTYPES = {"fp32": "f32", "fp64": "f64", "fp32_tc_bf16": "f32+bf16tc", "fp32_tc_fp16": "f32+fp16tc"}
+# ("x3": split operands, three tensor-core products per K step)
+DTYPES = {"fp32": "f32", "fp64": "f64", "fp32_tc_bf16": "f32+bf16tc", "fp32_tc_fp16": "f32+fp16tc",
+          "fp32_tc_bf16x3": "f32+bf16x3tc", "fp32_tc_fp16x3": "f32+fp16x3tc"}
 KERNELS = {"fp32": "stage_kernel<float, N={n}>", "fp64": "stage_kernel<double, N={n}>",
-           "fp32_tc_bf16": "tc_stage_kernel<{n}, bf16>", "fp32_tc_fp16": "tc_stage_kernel<{n}, fp16>"}
+           "fp32_tc_bf16": "tc_stage_kernel<{n}, bf16>", "fp32_tc_fp16": "tc_stage_kernel<{n}, fp16>",
+           "fp32_tc_bf16x3": "tc_stage_kernel<{n}, bf16, split>", "fp32_tc_fp16x3": "tc_stage_kernel<{n}, fp16, split>"}
+TC_PRECS = ("fp32_tc_bf16", "fp32_tc_fp16", "fp32_tc_bf16x3", "fp32_tc_fp16x3")
 
 
 def parse():
@@ -554,7 +558,7 @@ def main():
         # + the two mass kernels per step; the tensor-core path also permutes
         # u^n (base and low parts) into and out of its lane-contiguous layout
         # once per graph of up to 1024 steps
-        "gpu_launches": stage_launches_timed + (6 if "tc" in args.precision else 2) * args.steps,
+        "gpu_launches": stage_launches_timed + (6 if args.precision in TC_PRECS else 2) * args.steps,
         "clocks": clk.summary(),
         "mass_drift": (m1 - m0) / m0,
     }
@@ -574,7 +578,7 @@ def main():
                                "bytes_per_launch": leg["bytes_per_launch"], "launch_us": leg["launch_us"],
                                "workload": leg["workload"], "value": leg["value"]}
             out["roofline_timed_workload"] = dict(roofline_here, note="state arrays L2-resident across stages")
-            for tcp in ("fp32", "fp32_tc_bf16", "fp32_tc_fp16"):
+            for tcp in ("fp32",) + TC_PRECS:
                 if tcp != args.precision:
                     lv = streaming_leg(tcp, torch, stream, flush, make_prec)
                     tr = TRAFFIC.get((tcp, "r1"))
@@ -600,7 +604,7 @@ def main():
                                           "flops_per_dof": fpd}}
 
         # ---- the tensor-core precisions on the same workload (device-timed)
-        for tcp in ("fp32", "fp32_tc_bf16", "fp32_tc_fp16"):
+        for tcp in ("fp32",) + TC_PRECS:
             if tcp == args.precision:
                 continue
             stc = make(tcp)
@@ -678,7 +682,7 @@ def main():
                       "ms_per_step": 1e3 * e2e_s / args.steps, "mass": mass}
 
         # ---- at stated L2 error: (i) and (ii) on this workload and on 180x90 p = 3
-        precs = ["fp32", "fp32_tc_bf16", "fp32_tc_fp16"]
+        precs = ["fp32", *TC_PRECS]
         acc = {args.workload: accuracy_leg(args.workload, precs, lambda a, b, c: make_mesh(a, b, c, "fp64", 256),
                                            lambda a, b, c, d: make_mesh(a, b, c, d, 256))}
         if args.workload != "c2":
@@ -701,7 +705,7 @@ def main():
                                "seconds": leg["wall"], "cpu": cpu_model(),
                                "single_thread": {"value": single, "sample": "3 right-hand sides, 1 thread"}}
         errs = {}
-        for prec in sorted({"fp32", "fp64", "fp32_tc_bf16", "fp32_tc_fp16", args.precision}):
+        for prec in sorted({"fp32", "fp64", *TC_PRECS, args.precision}):
             sv = make(prec)
             sv.set_state(leg["u0"])
             sv.step(leg["nsteps"], leg["dt"])

@@ -61,8 +61,14 @@ typedef enum {
                                    edge points, volume integral and lift) as BF16 x BF16
                                    tensor-core GEMMs with FP32 accumulation; C_j^-1, fluxes
                                    and the RK update in FP32 */
-    DG_PREC_FP32_TC_FP16 = 3    /* the same with FP16 operands (momenta scaled by 2^-5
+    DG_PREC_FP32_TC_FP16 = 3,   /* the same with FP16 operands (momenta scaled by 2^-5
                                    into the FP16 range) */
+    DG_PREC_FP32_TC_BF16_SPLIT = 4, /* BF16 tensor cores with split operands: every operand
+                                   held as a pair hi + lo of BF16 values (lo = the rounded
+                                   residual) and every contraction taken as A_hi B_hi +
+                                   A_lo B_hi + A_hi B_lo in the FP32 accumulator, so the
+                                   rounding error per term falls from u to ~u^2 */
+    DG_PREC_FP32_TC_FP16_SPLIT = 5  /* the same with FP16 pairs (22 of FP32's 24 bits) */
 } dg_precision;
 
 typedef enum {

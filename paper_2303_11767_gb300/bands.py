@@ -64,16 +64,30 @@ def two_sum_merge(pairs):
     return s, c
 
 
+def bind_stream(band, stream):
+    """Make the band's library calls run on the torch stream `stream` (an
+    explicit, non-default stream: the library reads stream 0 as "its own
+    stream", which the exchange's copies would not be ordered with)."""
+    from . import dgswe
+
+    if stream.cuda_stream == 0:
+        raise ValueError("use a non-default torch.cuda.Stream for the bands")
+    band.set_option(dgswe.OPT_STREAM, stream.cuda_stream)
+
+
 class LocalExchange:
     """Every band in this process, in band order (south to north), on one
-    device; messages are device tensors copied in place.  The bands must share
-    one stream (DG_OPT_STREAM) so packs, copies and unpacks are ordered."""
+    device; messages are device tensors copied in place.  Every band is bound
+    to `stream`, so the packs, unpacks and stages of all bands run in one
+    order."""
 
-    def __init__(self, bands, torch, dtype):
+    def __init__(self, bands, torch, dtype, stream):
         self.bands = bands
+        for b in bands:
+            bind_stream(b, stream)
         n = bands[0].halo_len
-        dev = "cuda"
-        self.out = [[torch.empty(n, dtype=dtype, device=dev) for _ in range(2)] for _ in bands]
+        with torch.cuda.stream(stream):
+            self.out = [[torch.empty(n, dtype=dtype, device="cuda") for _ in range(2)] for _ in bands]
 
     def exchange(self):
         nb = len(self.bands)
@@ -94,16 +108,30 @@ class DistExchange:
     Each exchange sends the band's boundary rows to the ranks below and above
     and receives theirs, with torch.distributed point-to-point messages.  The
     band's buffers live on `device`; `wire` is where the messages travel from
-    ("cuda" for NCCL, "cpu" for gloo; host copies are made when they differ)."""
+    ("cuda" for NCCL, "cpu" for gloo; host copies are made when they differ).
+    A GPU band is bound to `stream` and the exchange's copies and messages
+    are issued on it (NCCL orders its work after the current stream)."""
 
-    def __init__(self, band, dist, rank, world, torch, dtype, device="cuda", wire="cuda"):
+    def __init__(self, band, dist, rank, world, torch, dtype, device="cuda", wire="cuda", stream=None):
         self.band, self.dist, self.rank, self.world, self.torch = band, dist, rank, world, torch
+        self.stream = stream
+        if device != "cpu":
+            if stream is None:
+                raise ValueError("a GPU band needs an explicit stream")
+            bind_stream(band, stream)
         n = band.halo_len
         self.dev = [torch.empty(n, dtype=dtype, device=device) for _ in range(4)]   # out S, out N, in S, in N
         self.wire = [t if wire == device else torch.empty(n, dtype=dtype, device=wire) for t in self.dev]
         self.has = (rank > 0, rank < world - 1)
 
     def exchange(self):
+        if self.stream is None:
+            self._exchange()
+        else:
+            with self.torch.cuda.stream(self.stream):
+                self._exchange()
+
+    def _exchange(self):
         b, d, w = self.band, self.dev, self.wire
         for side in (SOUTH, NORTH):
             if self.has[side]:

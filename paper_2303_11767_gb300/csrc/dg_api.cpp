@@ -119,7 +119,7 @@ struct dg_ctx {
     double href_given = 0;
     size_t row_len() const { return (size_t)nlon * 3 * nphi; }
     bool f32() const { return prec != DG_PREC_FP64; }                 // FP32 storage
-    bool tc() const { return prec == DG_PREC_FP32_TC_BF16 || prec == DG_PREC_FP32_TC_FP16; }
+    bool tc() const { return prec >= DG_PREC_FP32_TC_BF16 && prec <= DG_PREC_FP32_TC_FP16_SPLIT; }
 };
 
 namespace {
@@ -723,14 +723,14 @@ dg_status dg_set_option(dg_handle h, int key, long long value)
         return planar_unsupported(h, key == DG_OPT_PRECISION ? "a precision other than FP64"
                                      : key == DG_OPT_ALPHA_MODE ? "the global alpha mode"
                                                                 : "the well-balanced option");
-    if (h->band && ((key == DG_OPT_PRECISION && (value == DG_PREC_FP32_TC_BF16 || value == DG_PREC_FP32_TC_FP16)) ||
+    if (h->band && ((key == DG_OPT_PRECISION && value >= DG_PREC_FP32_TC_BF16) ||
                     (key == DG_OPT_ALPHA_MODE && value)))
         return fail(DG_EUNSUPPORTED, "a latitude band supports the FP64 and FP32 stages with the local Rusanov alpha");
     switch (key) {
     case DG_OPT_PRECISION: {
-        if (value < DG_PREC_FP64 || value > DG_PREC_FP32_TC_FP16) return fail(DG_EINVAL, "unknown precision %lld", value);
-        if ((value == DG_PREC_FP32_TC_BF16 || value == DG_PREC_FP32_TC_FP16) &&
-            dg_prepare_stage_tc(h->n, (int)(value - DG_PREC_FP32_TC_BF16)))
+        if (value < DG_PREC_FP64 || value > DG_PREC_FP32_TC_FP16_SPLIT)
+            return fail(DG_EINVAL, "unknown precision %lld", value);
+        if (value >= DG_PREC_FP32_TC_BF16 && dg_prepare_stage_tc(h->n, (int)(value - DG_PREC_FP32_TC_BF16)))
             return fail(DG_ECUDA, "tensor-core tables: %s", cudaGetErrorString(cudaGetLastError()));
         if (value == h->prec) return DG_OK;
         if (h->mlp) return fail(DG_EINVAL, "detach the learned source (dg_attach_mlp(h, NULL)) first");

@@ -73,26 +73,49 @@ constexpr int TC_TPE = 2;
 // chunks of A2 are never written and GEMM2 skips them (whole K steps, so CN
 // must be even).  The 16-bit row exchange of the theta faces (XN: N traces,
 // XS: S-face fluxes) lives there when it fits, else in its own region.
-template <int N>
+//
+// SPLIT: every operand is held as a pair (hi, lo) of 16-bit values, x ~ hi +
+// lo with lo the rounded residual x - hi, and every product A B is taken as
+// A_hi B_hi + A_lo B_hi + A_hi B_lo (three MMAs per K step into the same FP32
+// accumulator), which leaves an error of order u^2 instead of u per term.
+// The lo operands follow the hi ones (B1L, B2L; A lo = A hi + LO1 for GEMM1,
+// + LO2 for GEMM2).  The theta-face exchange carries FP32 values: XN in its
+// own region, XS (read as fluxes into the A2 pairs) in field h's unused S
+// chunks of the hi (rows 0, 1) and lo (rows 2, 3) operands when they fit.
+// At degree 4 the split plan needs 223 KB: one CTA per SM.
+template <int N, bool SPLIT = false>
 struct TcSmem {
     using GE = TcGeo<N>;
+    static constexpr int NB = SPLIT ? 2 : 1;   // copies of each operand (hi, lo)
     static constexpr uint32_t B1 = 0;
     static constexpr uint32_t SZ_B1 = GE::N1 * GE::K1 * 2;
-    static constexpr uint32_t B2 = (SZ_B1 + 127) / 128 * 128;
+    static constexpr uint32_t B1L = B1 + SZ_B1;
+    static constexpr uint32_t B2 = (NB * SZ_B1 + 127) / 128 * 128;
     static constexpr uint32_t SZ_B2 = GE::N2 * GE::K2 * 2;
-    static constexpr uint32_t A = (B2 + SZ_B2 + 1023) / 1024 * 1024;
+    static constexpr uint32_t B2L = B2 + SZ_B2;
+    static constexpr uint32_t A = (B2 + NB * SZ_B2 + 1023) / 1024 * 1024;
     static constexpr uint32_t SZ_A1 = 3 * GE::K1C * CH;
     static constexpr uint32_t SZ_A1H = 3 * GE::K1C * CH;
     static constexpr uint32_t SZ_A2 = 3 * GE::KC2 * CH;
-    static constexpr uint32_t SZ_A = SZ_A1 + SZ_A1H > SZ_A2 ? SZ_A1 + SZ_A1H : SZ_A2;
+    static constexpr uint32_t LO1 = SZ_A1 + SZ_A1H;   // GEMM1 lo operands after the hi ones
+    static constexpr uint32_t LO2 = SZ_A2;            // GEMM2 lo operand after the hi one
+    static constexpr uint32_t SZ_A = NB * (SZ_A1 + SZ_A1H > SZ_A2 ? SZ_A1 + SZ_A1H : SZ_A2);
     static constexpr bool SKIP_S0 = GE::CN % 2 == 0;
-    static constexpr uint32_t SZ_X = 4 * 32 * 3 * N * 2;   // one 16-bit exchange array
-    static constexpr bool X_IN_S0 = SKIP_S0 && 2 * SZ_X <= GE::CN * CH;
-    static constexpr uint32_t XN = X_IN_S0 ? A + 2 * GE::CN * CH : A + SZ_A;
-    static constexpr uint32_t XS = XN + SZ_X;
-    static constexpr uint32_t BYTES = A + SZ_A + (X_IN_S0 ? 0 : 2 * SZ_X);
+    // 16-bit exchange (one array) / FP32 exchange (one array, or half of one)
+    static constexpr uint32_t SZ_X = SPLIT ? 4 * 32 * 3 * N * 4 : 4 * 32 * 3 * N * 2;
+    static constexpr bool X_IN_S0 = SKIP_S0 && (SPLIT ? SZ_X / 2 : 2 * SZ_X) <= GE::CN * CH;
+    // non-split: XN and XS together in the S chunks of field h, else after A;
+    // split: XN after A, XS halves in the S chunks of field h (hi and lo) or after XN
+    static constexpr uint32_t S0 = A + 2 * GE::CN * CH;
+    static constexpr uint32_t XN = SPLIT ? A + SZ_A : X_IN_S0 ? S0 : A + SZ_A;
+    static constexpr uint32_t XS = SPLIT ? (X_IN_S0 ? S0 : XN + SZ_X) : XN + SZ_X;
+    static constexpr uint32_t XS_HI = SPLIT && X_IN_S0 ? S0 + LO2 : XS + SZ_X / 2;   // rows 2, 3
+    static constexpr uint32_t BYTES =
+        A + SZ_A + (SPLIT ? (X_IN_S0 ? SZ_X : 2 * SZ_X) : (X_IN_S0 ? 0 : 2 * SZ_X));
+    static constexpr int CTAS = BYTES <= 113 * 1024 ? 2 : 1;   // CTAs per SM
     static_assert(3 * GE::N1 + 48 <= (int)TMEM_COLS, "tensor-memory columns");
-    static_assert(BYTES <= 113 * 1024, "two CTAs per SM");
+    static_assert(BYTES <= 227 * 1024, "shared memory of one CTA");
+    static_assert(SPLIT || CTAS == 2, "two CTAs per SM");
 };
 
 template <typename OpT>
@@ -115,6 +138,12 @@ struct Op<__nv_bfloat16> {
         std::memcpy(&u, &v, 2);
         return u;
     }
+    static float host_value(uint16_t u)
+    {
+        __nv_bfloat16 v;
+        std::memcpy(&v, &u, 2);
+        return __bfloat162float(v);
+    }
 };
 template <>
 struct Op<__half> {
@@ -135,6 +164,12 @@ struct Op<__half> {
         uint16_t u;
         std::memcpy(&u, &v, 2);
         return u;
+    }
+    static float host_value(uint16_t u)
+    {
+        __half v;
+        std::memcpy(&v, &u, 2);
+        return __half2float(v);
     }
 };
 
@@ -260,15 +295,30 @@ __device__ __forceinline__ void put_chunk(unsigned char *p, const float *v)
     *reinterpret_cast<uint4 *>(p) = u;
 }
 
+// The pair (hi, lo) of 8 values: hi = the rounded value, lo = the rounded
+// residual v - hi; written to p and p + lo_off.
+template <typename OpT>
+__device__ __forceinline__ void put_chunk_split(unsigned char *p, uint32_t lo_off, const float *v)
+{
+    float hi[8], lo[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        hi[k] = Op<OpT>::from16(Op<OpT>::to16(v[k]));
+        lo[k] = v[k] - hi[k];
+    }
+    put_chunk<OpT>(p, hi);
+    put_chunk<OpT>(p + lo_off, lo);
+}
+
 // ------------------------------------------------------------ stage kernel --
 
-template <int N, typename OpT>
-__global__ void __launch_bounds__(128 * TC_TPE, 2) tc_stage_kernel(const StageArgs<float> A,
+template <int N, typename OpT, bool SPLIT>
+__global__ void __launch_bounds__(128 * TC_TPE, TcSmem<N, SPLIT>::CTAS) tc_stage_kernel(const StageArgs<float> A,
                                                                    const uint4 *__restrict__ gB1,
                                                                    const uint4 *__restrict__ gB2)
 {
     using GE = TcGeo<N>;
-    using SM = TcSmem<N>;
+    using SM = TcSmem<N, SPLIT>;
     constexpr int NP = GE::NP, CN = GE::CN, NC = GE::NC, K1C = GE::K1C, N1 = GE::N1, N2 = GE::N2, EW = GE::EW,
                   KC2 = GE::KC2, TRC = GE::TRC;
     constexpr int NT = 128 * TC_TPE;
@@ -302,13 +352,26 @@ __global__ void __launch_bounds__(128 * TC_TPE, 2) tc_stage_kernel(const StageAr
     // memory, the completion barrier, the two basis operands
     if (w == 0) tmem_alloc(smem_u32(&tslot));
     if (tid == 0) mbar_init(smem_u32(&mbar));
-    for (int c = tid; c < (int)(SM::SZ_B1 / 16); c += NT) reinterpret_cast<uint4 *>(sm + SM::B1)[c] = __ldg(gB1 + c);
-    for (int c = tid; c < (int)(SM::SZ_B2 / 16); c += NT) reinterpret_cast<uint4 *>(sm + SM::B2)[c] = __ldg(gB2 + c);
+    // (hi, then lo in SPLIT mode)
+    for (int c = tid; c < (int)(SM::NB * SM::SZ_B1 / 16); c += NT)
+        reinterpret_cast<uint4 *>(sm + SM::B1)[c] = __ldg(gB1 + c);
+    for (int c = tid; c < (int)(SM::NB * SM::SZ_B2 / 16); c += NT)
+        reinterpret_cast<uint4 *>(sm + SM::B2)[c] = __ldg(gB2 + c);
     dgk::pdl_wait();
     if (A.galpha) {
         ga_l = __ldg(A.galpha);
         ga_t = __ldg(A.galpha + 1);
     }
+
+    // operand rows: one 16-bit value, or the (hi, lo) pair in SPLIT mode
+    auto put_a1 = [&](unsigned char *dst, const float *v) {
+        if constexpr (SPLIT) put_chunk_split<OpT>(dst, SM::LO1, v);
+        else put_chunk<OpT>(dst, v);
+    };
+    auto put_a2 = [&](unsigned char *dst, const float *v) {
+        if constexpr (SPLIT) put_chunk_split<OpT>(dst, SM::LO2, v);
+        else put_chunk<OpT>(dst, v);
+    };
 
     // ---- S0: 8 modes (chunk c) of one field of the stage state u = base + inc
     //      of one element -> its row of a GEMM1 operand (zeros where missing)
@@ -330,7 +393,7 @@ __global__ void __launch_bounds__(128 * TC_TPE, 2) tc_stage_kernel(const StageAr
 #pragma unroll
             for (int k = 0; k < 8; ++k) v[k] *= s;
         }
-        put_chunk<OpT>(dst + c * CH, v);
+        put_a1(dst + c * CH, v);
     };
     // the low parts and the RK4 accumulator are read only by the epilogue:
     // start moving this thread's share of them into L2 now
@@ -375,14 +438,24 @@ __global__ void __launch_bounds__(128 * TC_TPE, 2) tc_stage_kernel(const StageAr
         const uint32_t b1 = smem_u32(sm + SM::B1);
         constexpr uint32_t LB1 = N1 * 16;
         constexpr uint32_t id1 = idesc<Op<OpT>::bf16>(128, N1), idh = idesc<Op<OpT>::bf16>(128, 16);
+        // A B, or A_hi B_hi + A_lo B_hi + A_hi B_lo in SPLIT mode
+        auto mma3 = [&](uint32_t d, uint32_t a, uint32_t lo_a, uint32_t b, uint32_t lo_b, uint32_t lbo_b,
+                        uint32_t id, uint32_t acc) {
+            mma(d, sdesc(a, CH, 128), sdesc(b, lbo_b, 128), id, acc);
+            if constexpr (SPLIT) {
+                mma(d, sdesc(a + lo_a, CH, 128), sdesc(b, lbo_b, 128), id, 1);
+                mma(d, sdesc(a, CH, 128), sdesc(b + lo_b, lbo_b, 128), id, 1);
+            }
+        };
+        constexpr uint32_t LOB1 = SM::B1L - SM::B1;
         for (int f = 0; f < 3; ++f)
             for (int s = 0; s < K1C / 2; ++s)
-                mma(tbase + (uint32_t)(f * N1), sdesc(a0 + (uint32_t)(f * K1C + 2 * s) * CH, CH, 128),
-                    sdesc(b1 + 2 * s * LB1, LB1, 128), id1, s > 0);
+                mma3(tbase + (uint32_t)(f * N1), a0 + (uint32_t)(f * K1C + 2 * s) * CH, SM::LO1,
+                     b1 + 2 * s * LB1, LOB1, LB1, id1, s > 0);
         for (int f = 0; f < 3; ++f)
             for (int s = 0; s < K1C / 2; ++s)
-                mma(tbase + (uint32_t)(3 * N1 + 16 * f), sdesc(a0 + SM::SZ_A1 + (uint32_t)(f * K1C + 2 * s) * CH, CH, 128),
-                    sdesc(b1 + NC * 16 + 2 * s * LB1, LB1, 128), idh, s > 0);
+                mma3(tbase + (uint32_t)(3 * N1 + 16 * f), a0 + SM::SZ_A1 + (uint32_t)(f * K1C + 2 * s) * CH, SM::LO1,
+                     b1 + NC * 16 + 2 * s * LB1, LOB1, LB1, idh, s > 0);
         mma_commit(mb);
     }
     if (!mbar_wait(mb, 0)) st |= DG_STATUS_TIMEOUT;
@@ -392,8 +465,30 @@ __global__ void __launch_bounds__(128 * TC_TPE, 2) tc_stage_kernel(const StageAr
     const uint32_t tl = tbase + ((uint32_t)(32 * q4) << 16);
     unsigned char *const a2row = opA + rowoff;
     auto a2 = [&](int f, int c) { return a2row + (uint32_t)(f * KC2 + c) * CH; };
+    // theta-face row exchange: N traces (XN) and S-face fluxes (XS) of tile
+    // row q, field f, point k, lane l; 16-bit values (unscaled, as the
+    // operands), or FP32 in SPLIT mode (XS rows 2, 3 in a second half)
     uint16_t *XN = reinterpret_cast<uint16_t *>(sm + SM::XN);
     uint16_t *XS = reinterpret_cast<uint16_t *>(sm + SM::XS);
+    auto xn_put = [&](int q, int f, int k, float v) {
+        if constexpr (SPLIT) reinterpret_cast<float *>(sm + SM::XN)[((q * 3 + f) * N + k) * 32 + l] = v;
+        else XN[((q * 3 + f) * N + k) * 32 + l] = Op<OpT>::to16(v * (f == 0 ? 1.0f : MS));
+    };
+    auto xn_get = [&](int q, int f, int k) -> float {
+        if constexpr (SPLIT) return reinterpret_cast<const float *>(sm + SM::XN)[((q * 3 + f) * N + k) * 32 + l];
+        else return Op<OpT>::from16(XN[((q * 3 + f) * N + k) * 32 + l]) * (f == 0 ? 1.0f : IMS);
+    };
+    auto xs_slot = [&](int q, int f, int k) -> float * {
+        return reinterpret_cast<float *>(sm + (q < 2 ? SM::XS : SM::XS_HI)) + (((q & 1) * 3 + f) * N + k) * 32 + l;
+    };
+    auto xs_put = [&](int q, int f, int k, float v) {
+        if constexpr (SPLIT) *xs_slot(q, f, k) = v;
+        else XS[((q * 3 + f) * N + k) * 32 + l] = Op<OpT>::to16(v);
+    };
+    auto xs_get = [&](int q, int f, int k) -> float {
+        if constexpr (SPLIT) return *xs_slot(q, f, k);
+        else return Op<OpT>::from16(XS[((q * 3 + f) * N + k) * 32 + l]);
+    };
 
     // own traces of 3 fields, columns [NC + c0, NC + c0 + 2N): (S, N) for
     // c0 = 0, (W, E) for c0 = 2N; unscaled
@@ -453,19 +548,20 @@ __global__ void __launch_bounds__(128 * TC_TPE, 2) tc_stage_kernel(const StageAr
                 if (EW == 4) c0[4 + k] = efE[f][k];
                 else c1[k] = efE[f][k];
             }
-            put_chunk<OpT>(a2(f, 3 * CN), c0);
-            if (EW == 8) put_chunk<OpT>(a2(f, 3 * CN + 1), c1);
+            put_a2(a2(f, 3 * CN), c0);
+            if (EW == 8) put_a2(a2(f, 3 * CN + 1), c1);
 #pragma unroll
             for (int c = 3 * CN + GE::CE; c < KC2; ++c) {   // zero K padding
                 float z[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-                put_chunk<OpT>(a2(f, c), z);
+                put_a2(a2(f, c), z);
             }
         }
     }
 
     // ---- S5 theta faces (part PN) through the 16-bit row exchange (the
     //      faces' fluxes are rounded to the operand type in A2 anyway; the
-    //      neighbour's trace carries one rounding of the operand type): every
+    //      neighbour's trace carries one rounding of the operand type; FP32
+    //      in SPLIT mode, where A2 holds the fluxes to ~u^2): every
     //      element evaluates its S edge; its N edge is the S edge of the
     //      element above (for the top row of a full tile: evaluated against
     //      the halo).  Only part PN's warps meet at these barriers; the other
@@ -496,7 +592,7 @@ __global__ void __launch_bounds__(128 * TC_TPE, 2) tc_stage_kernel(const StageAr
         for (int f = 0; f < 3; ++f)
 #pragma unroll
             for (int k = 0; k < N; ++k)
-                XN[((q4 * 3 + f) * N + k) * 32 + l] = Op<OpT>::to16(tsn[f][N + k] * (f == 0 ? 1.0f : MS));
+                xn_put(q4, f, k, tsn[f][N + k]);
         part_barrier();
     }
     float efS[3][N];
@@ -508,8 +604,7 @@ __global__ void __launch_bounds__(128 * TC_TPE, 2) tc_stage_kernel(const StageAr
             float Sq[3], Nq[3], o[3];
 #pragma unroll
             for (int f = 0; f < 3; ++f) {
-                Sq[f] = q4 > 0 ? Op<OpT>::from16(XN[(((q4 - 1) * 3 + f) * N + k) * 32 + l]) * (f == 0 ? 1.0f : IMS)
-                               : halo[f][k];
+                Sq[f] = q4 > 0 ? xn_get(q4 - 1, f, k) : halo[f][k];
                 Nq[f] = tsn[f][k];
             }
             dgk::rusanov_th(Sq, Nq, href, gg, cgs, o, ss, ga_t);
@@ -520,7 +615,7 @@ __global__ void __launch_bounds__(128 * TC_TPE, 2) tc_stage_kernel(const StageAr
 #pragma unroll
         for (int f = 0; f < 3; ++f)
 #pragma unroll
-            for (int k = 0; k < N; ++k) XS[((q4 * 3 + f) * N + k) * 32 + l] = Op<OpT>::to16(efS[f][k]);
+            for (int k = 0; k < N; ++k) xs_put(q4, f, k, efS[f][k]);
         part_barrier();
     }
     float efN[3][N];
@@ -529,7 +624,7 @@ __global__ void __launch_bounds__(128 * TC_TPE, 2) tc_stage_kernel(const StageAr
 #pragma unroll
             for (int f = 0; f < 3; ++f)
 #pragma unroll
-                for (int k = 0; k < N; ++k) efN[f][k] = Op<OpT>::from16(XS[(((q4 + 1) * 3 + f) * N + k) * 32 + l]);
+                for (int k = 0; k < N; ++k) efN[f][k] = xs_get(q4 + 1, f, k);
         } else if (j0 + q4 + 1 >= A.nlat) {
 #pragma unroll
             for (int f = 0; f < 3; ++f)
@@ -565,10 +660,10 @@ __global__ void __launch_bounds__(128 * TC_TPE, 2) tc_stage_kernel(const StageAr
                 if (EW == 4) c0[4 + k] = efN[f][k];
                 else c1[k] = efN[f][k];
             }
-            if (EW == 4) put_chunk<OpT>(a2(f, 3 * CN + 1), c0);
+            if (EW == 4) put_a2(a2(f, 3 * CN + 1), c0);
             else {
-                put_chunk<OpT>(a2(f, 3 * CN + 2), c0);
-                put_chunk<OpT>(a2(f, 3 * CN + 3), c1);
+                put_a2(a2(f, 3 * CN + 2), c0);
+                put_a2(a2(f, 3 * CN + 3), c1);
             }
         }
     }
@@ -616,9 +711,9 @@ __global__ void __launch_bounds__(128 * TC_TPE, 2) tc_stage_kernel(const StageAr
             }
 #pragma unroll
             for (int f = 0; f < 3; ++f) {
-                put_chunk<OpT>(a2(f, g), Fv[f]);
-                put_chunk<OpT>(a2(f, CN + g), Gq[f]);
-                if (f > 0 || !SM::SKIP_S0) put_chunk<OpT>(a2(f, 2 * CN + g), Sv[f]);
+                put_a2(a2(f, g), Fv[f]);
+                put_a2(a2(f, CN + g), Gq[f]);
+                if (f > 0 || !SM::SKIP_S0) put_a2(a2(f, 2 * CN + g), Sv[f]);
             }
         }
         if (interior) st_int |= sq;
@@ -633,11 +728,17 @@ __global__ void __launch_bounds__(128 * TC_TPE, 2) tc_stage_kernel(const StageAr
         const uint32_t b2 = smem_u32(sm + SM::B2);
         constexpr uint32_t LB2 = N2 * 16;
         constexpr uint32_t id2 = idesc<Op<OpT>::bf16>(128, N2);
+        constexpr uint32_t LOB2 = SM::B2L - SM::B2;
         for (int f = 0; f < 3; ++f)
             for (int s = 0; s < KC2 / 2; ++s) {
                 if (f == 0 && SM::SKIP_S0 && 2 * s >= 2 * CN && 2 * s < 3 * CN) continue;   // S_h = 0
-                mma(tbase + (uint32_t)(f * N1), sdesc(a0 + (uint32_t)(f * KC2 + 2 * s) * CH, CH, 128),
-                    sdesc(b2 + 2 * s * LB2, LB2, 128), id2, s > 0);
+                const uint32_t d = tbase + (uint32_t)(f * N1), a = a0 + (uint32_t)(f * KC2 + 2 * s) * CH;
+                const uint32_t b = b2 + 2 * s * LB2;
+                mma(d, sdesc(a, CH, 128), sdesc(b, LB2, 128), id2, s > 0);
+                if constexpr (SPLIT) {
+                    mma(d, sdesc(a + SM::LO2, CH, 128), sdesc(b, LB2, 128), id2, 1);
+                    mma(d, sdesc(a, CH, 128), sdesc(b + LOB2, LB2, 128), id2, 1);
+                }
             }
         mma_commit(mb);
     }
@@ -818,8 +919,10 @@ __global__ void permute_kernel(const float *__restrict__ src, float *__restrict_
 
 // Operand B of both GEMMs in the canonical K-major layout: element (r, k) of
 // an R-row operand at byte (k / 8) * R * 16 + r * 16 + (k % 8) * 2.
+// SPLIT: each table is followed by its lo part, the rounded residual of the
+// FP32 value after the hi rounding.
 template <int N, typename OpT>
-void build_tables(std::vector<uint16_t> &b1, std::vector<uint16_t> &b2)
+void build_tables(std::vector<uint16_t> &b1, std::vector<uint16_t> &b2, bool split)
 {
     using GE = TcGeo<N>;
     constexpr int NP = GE::NP, NC = GE::NC, K1 = GE::K1, N1 = GE::N1, N2 = GE::N2, K2 = GE::K2, EW = GE::EW,
@@ -869,11 +972,16 @@ void build_tables(std::vector<uint16_t> &b1, std::vector<uint16_t> &b2)
         }
     }
     (void)CN;
-    auto canon = [](const std::vector<double> &m, int R, int K, std::vector<uint16_t> &out) {
-        out.assign((size_t)R * K, 0);
+    auto canon = [split](const std::vector<double> &m, int R, int K, std::vector<uint16_t> &out) {
+        const size_t sz = (size_t)R * K;
+        out.assign(split ? 2 * sz : sz, 0);
         for (int r = 0; r < R; ++r)
-            for (int k = 0; k < K; ++k)
-                out[(size_t)(k / 8) * R * 8 + (size_t)r * 8 + (k % 8)] = Op<OpT>::host_bits((float)m[(size_t)r * K + k]);
+            for (int k = 0; k < K; ++k) {
+                const size_t o = (size_t)(k / 8) * R * 8 + (size_t)r * 8 + (k % 8);
+                const float v = (float)m[(size_t)r * K + k];
+                out[o] = Op<OpT>::host_bits(v);
+                if (split) out[sz + o] = Op<OpT>::host_bits(v - Op<OpT>::host_value(out[o]));
+            }
     };
     canon(m1, N1, K1, b1);
     canon(m2, N2, K2, b2);
@@ -886,8 +994,9 @@ struct TabSet {
 // shared-memory opt-in is set; handles on several host threads share them,
 // so every access holds g_tc_mu
 std::mutex g_tc_mu;
-TabSet g_tabs[64][DG_MAXN][2];
-unsigned long long g_attr[DG_MAXN][2];
+// op: 0 BF16, 1 FP16, 2 BF16 split, 3 FP16 split
+TabSet g_tabs[64][DG_MAXN][4];
+unsigned long long g_attr[DG_MAXN][4];
 unsigned long long g_check_attr[DG_MAXN][2];
 
 template <int N, typename OpT>
@@ -896,7 +1005,7 @@ int tables_for(int dev, int op, TabSet &out)   // caller holds g_tc_mu
     TabSet &t = g_tabs[dev][N - 1][op];
     if (!t.b1) {
         std::vector<uint16_t> b1, b2;
-        build_tables<N, OpT>(b1, b2);
+        build_tables<N, OpT>(b1, b2, op >= 2);
         uint4 *d1 = nullptr, *d2 = nullptr;
         if (cudaMalloc(&d1, b1.size() * 2) != cudaSuccess) return 1;
         if (cudaMalloc(&d2, b2.size() * 2) != cudaSuccess) {
@@ -918,16 +1027,16 @@ int tables_for(int dev, int op, TabSet &out)   // caller holds g_tc_mu
 
 // Tables and the shared-memory opt-in of one (degree, operand type) on the
 // current device; allocates and copies, so it must run outside stream capture.
-template <int N, typename OpT>
+template <int N, typename OpT, bool SPLIT>
 int prepare_tc(int op, TabSet &t)
 {
-    using SM = TcSmem<N>;
+    using SM = TcSmem<N, SPLIT>;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 1;
     std::lock_guard<std::mutex> lock(g_tc_mu);
     if (tables_for<N, OpT>(dev, op, t)) return 1;
     if (!(g_attr[N - 1][op] >> dev & 1ull)) {
-        if (cudaFuncSetAttribute(tc_stage_kernel<N, OpT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        if (cudaFuncSetAttribute(tc_stage_kernel<N, OpT, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)SM::BYTES) != cudaSuccess)
             return 1;
         g_attr[N - 1][op] |= 1ull << dev;
@@ -935,10 +1044,10 @@ int prepare_tc(int op, TabSet &t)
     return 0;
 }
 
-template <int N, typename OpT>
+template <int N, typename OpT, bool SPLIT>
 int launch_tc(int op, const StageArgs<float> &a, cudaStream_t s)
 {
-    using SM = TcSmem<N>;
+    using SM = TcSmem<N, SPLIT>;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 1;
     TabSet t;
@@ -948,7 +1057,7 @@ int launch_tc(int op, const StageArgs<float> &a, cudaStream_t s)
         if (!t.b1 || !(g_attr[N - 1][op] >> dev & 1ull)) return 1;   // dg_prepare_stage_tc was not called
     }
     dim3 grid((a.nlon + TC_TW - 1) / TC_TW, (a.nlat + 3) / 4);
-    if (dgk::launch_pdl(tc_stage_kernel<N, OpT>, grid, dim3(128 * TC_TPE), SM::BYTES, s, a,
+    if (dgk::launch_pdl(tc_stage_kernel<N, OpT, SPLIT>, grid, dim3(128 * TC_TPE), SM::BYTES, s, a,
                         (const uint4 *)t.b1, (const uint4 *)t.b2) != cudaSuccess)
         return 1;
     return cudaPeekAtLastError() == cudaSuccess ? 0 : 1;
@@ -988,50 +1097,51 @@ int check_tc(int op, const float *a, float *d, int *n1, int *k1, cudaStream_t s)
 
 }  // namespace
 
-int dg_prepare_stage_tc(int n, int op)
+namespace {
+// (degree, operand mode) -> the instantiation: op 0 BF16, 1 FP16, 2 BF16
+// split, 3 FP16 split
+template <template <int, typename, bool> class F, typename... Args>
+int dispatch_tc(int n, int op, Args... args)
 {
-    TabSet t;
-    if (op == 0) {
-        switch (n) {
-        case 1: return prepare_tc<1, __nv_bfloat16>(0, t);
-        case 2: return prepare_tc<2, __nv_bfloat16>(0, t);
-        case 3: return prepare_tc<3, __nv_bfloat16>(0, t);
-        case 4: return prepare_tc<4, __nv_bfloat16>(0, t);
-        case 5: return prepare_tc<5, __nv_bfloat16>(0, t);
-        default: return 1;
-        }
+#define DG_TC_CASES(OPT, SPL)                                         \
+    switch (n) {                                                      \
+    case 1: return F<1, OPT, SPL>::run(op, args...);                  \
+    case 2: return F<2, OPT, SPL>::run(op, args...);                  \
+    case 3: return F<3, OPT, SPL>::run(op, args...);                  \
+    case 4: return F<4, OPT, SPL>::run(op, args...);                  \
+    case 5: return F<5, OPT, SPL>::run(op, args...);                  \
+    default: return 1;                                                \
     }
-    switch (n) {
-    case 1: return prepare_tc<1, __half>(1, t);
-    case 2: return prepare_tc<2, __half>(1, t);
-    case 3: return prepare_tc<3, __half>(1, t);
-    case 4: return prepare_tc<4, __half>(1, t);
-    case 5: return prepare_tc<5, __half>(1, t);
+    switch (op) {
+    case 0: DG_TC_CASES(__nv_bfloat16, false)
+    case 1: DG_TC_CASES(__half, false)
+    case 2: DG_TC_CASES(__nv_bfloat16, true)
+    case 3: DG_TC_CASES(__half, true)
     default: return 1;
     }
+#undef DG_TC_CASES
 }
+
+template <int N, typename OpT, bool SPLIT>
+struct PrepareTc {
+    static int run(int op)
+    {
+        TabSet t;
+        return prepare_tc<N, OpT, SPLIT>(op, t);
+    }
+};
+
+template <int N, typename OpT, bool SPLIT>
+struct LaunchTc {
+    static int run(int op, const StageArgs<float> *a, cudaStream_t s) { return launch_tc<N, OpT, SPLIT>(op, *a, s); }
+};
+}  // namespace
+
+int dg_prepare_stage_tc(int n, int op) { return dispatch_tc<PrepareTc>(n, op); }
 
 int dg_launch_stage_tc(int n, int op, const StageArgs<float> &a, void *stream)
 {
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
-    if (op == 0) {
-        switch (n) {
-        case 1: return launch_tc<1, __nv_bfloat16>(0, a, s);
-        case 2: return launch_tc<2, __nv_bfloat16>(0, a, s);
-        case 3: return launch_tc<3, __nv_bfloat16>(0, a, s);
-        case 4: return launch_tc<4, __nv_bfloat16>(0, a, s);
-        case 5: return launch_tc<5, __nv_bfloat16>(0, a, s);
-        default: return 1;
-        }
-    }
-    switch (n) {
-    case 1: return launch_tc<1, __half>(1, a, s);
-    case 2: return launch_tc<2, __half>(1, a, s);
-    case 3: return launch_tc<3, __half>(1, a, s);
-    case 4: return launch_tc<4, __half>(1, a, s);
-    case 5: return launch_tc<5, __half>(1, a, s);
-    default: return 1;
-    }
+    return dispatch_tc<LaunchTc>(n, op, &a, static_cast<cudaStream_t>(stream));
 }
 
 int dg_tc_gemm_check(int n, int op, const float *a, float *d, int *n1, int *k1, void *stream)

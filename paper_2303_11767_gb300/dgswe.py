@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(HERE, "libdgswe.so")
 DG_OK, DG_EINVAL, DG_ENOMEM, DG_ECUDA, DG_ENONFINITE, DG_ENONPHYSICAL, DG_ETIMEOUT, DG_EUNSUPPORTED = range(8)
 STATUS_NAMES = {0: "DG_OK", 1: "DG_EINVAL", 2: "DG_ENOMEM", 3: "DG_ECUDA", 4: "DG_ENONFINITE",
                 5: "DG_ENONPHYSICAL", 6: "DG_ETIMEOUT", 7: "DG_EUNSUPPORTED"}
-PREC = {"fp64": 0, "fp32": 1, "fp32_tc_bf16": 2, "fp32_tc_fp16": 3}
+PREC = {"fp64": 0, "fp32": 1, "fp32_tc_bf16": 2, "fp32_tc_fp16": 3, "fp32_tc_bf16x3": 4, "fp32_tc_fp16x3": 5}
 OPT_PRECISION, OPT_RK_ORDER, OPT_CHECK_FINITE, OPT_ALPHA_MODE, OPT_STREAM, OPT_STEPS_PER_GRAPH = 1, 2, 3, 4, 5, 6
 OPT_TILE_ROWS, OPT_BLOCKS_PER_SM, OPT_WELL_BALANCED = 7, 8, 9
 

@@ -20,16 +20,15 @@ NTHREADS = os.cpu_count() or 1
 
 
 def _run_bands(u0, nlon, nlat, p, prec, nb, nsteps, dt, rk, torch):
-    stream = torch.cuda.current_stream()
+    stream = torch.cuda.Stream()
     rows = [bands.band_rows(nlat, nb, k) for k in range(nb)]
     bs = [dgswe.Solver.band(nlon, nlat, jb, je, p, R, G, OMEGA, precision=prec, rk_order=rk) for jb, je in rows]
+    ex = bands.LocalExchange(bs, torch, torch.float64 if prec == "fp64" else torch.float32, stream)
     href = bands.reference_depth(None, u0[:, :, 0, 0], 0, 1, torch)
     for b, (jb, je) in zip(bs, rows):
-        b.set_option(dgswe.OPT_STREAM, stream.cuda_stream)
         if prec != "fp64":
             b.set_reference_depth(href)
         b.set_state(u0[jb:je])
-    ex = bands.LocalExchange(bs, torch, torch.float64 if prec == "fp64" else torch.float32)
     bands.advance(bs, ex, nsteps, dt, rk)
     out = np.concatenate([b.get_state() for b in bs], axis=0)
     mass = bands.global_mass(None, bands.two_sum_merge([b.mass_pair() for b in bs]), R, torch)
@@ -42,7 +41,6 @@ def _run_bands(u0, nlon, nlat, p, prec, nb, nsteps, dt, rk, torch):
 
 def _whole(u0, nlon, nlat, p, prec, nsteps, dt, rk, torch):
     with dgswe.Solver(nlon, nlat, p, R, G, OMEGA, precision=prec, rk_order=rk) as s:
-        s.set_option(dgswe.OPT_STREAM, torch.cuda.current_stream().cuda_stream)
         s.set_state(u0)
         dt_whole = s.max_dt(0.1)
         s.step(nsteps, dt)
@@ -95,6 +93,8 @@ def test_band_refuses_what_needs_the_whole_mesh():
         with pytest.raises(dgswe.DGError) as e:
             call()
         assert e.value.status == dgswe.DG_EUNSUPPORTED
+    with pytest.raises(ValueError):                  # the library's own stream is not ordered with torch's
+        bands.LocalExchange([b], torch, torch.float64, torch.cuda.default_stream())
     # the pole side of a polar band has no ghost row
     s = dgswe.Solver.band(20, 10, 0, 5, 1, R, G, OMEGA)
     s.set_state(np.concatenate([u, u[:1]], axis=0))

@@ -12,6 +12,13 @@ measure as the FP32 / FP64 parity tests).  A state after K steps of size dt
 stays within K dt C u |S| of the oracle's, plus the FP32 state tolerance.
 The contraction itself (exact products of rounded operands, FP32 sums of at
 most 32 terms) matches an FP64 product of the rounded operands to 1e-5.
+
+Split operands (precisions fp32_tc_bf16x3, fp32_tc_fp16x3): each operand is
+a pair hi + lo of the 16-bit type, which represents it to u^2, and each
+product is A_hi B_hi + A_lo B_hi + A_hi B_lo; the neglected A_lo B_lo is of
+order u^2 too.  Their tendencies are held to C u^2 S plus the FP32
+tendency tolerance (1e-6 S), and their states to the plain per-field FP32
+tolerance 1e-5 (relative L2 and max), with no derived allowance.
 """
 import os
 
@@ -27,6 +34,7 @@ torch = pytest.importorskip("torch")
 
 R, G, OMEGA = synth.EARTH_RADIUS, 9.80616, 7.292e-5
 OPS = {"fp32_tc_bf16": (0, 2.0 ** -9, torch.bfloat16), "fp32_tc_fp16": (1, 2.0 ** -12, torch.float16)}
+SPLIT = {"fp32_tc_bf16x3": 2.0 ** -18, "fp32_tc_fp16x3": 2.0 ** -24}   # u^2 of the pair
 C = 8.0
 _cache = {}
 
@@ -215,10 +223,12 @@ def test_first_use_is_a_captured_step():
     assert r.stdout.split() == ["ok", "48"]
 
 
-@pytest.mark.parametrize("prec", ["fp32", "fp32_tc_bf16", "fp32_tc_fp16"])
+@pytest.mark.parametrize("prec", ["fp32", "fp32_tc_bf16", "fp32_tc_fp16", "fp32_tc_bf16x3", "fp32_tc_fp16x3"])
 def test_precision_config_360x180_p4_500_steps(prec):
     """The precision configuration: 360x180, degree 4, 500 SSP-RK3 steps at
-    CFL 0.1, per-field relative L2 and max error against the FP64 oracle."""
+    CFL 0.1, per-field relative L2 and max error against the FP64 oracle.
+    FP32 and the split tensor-core precisions: within the plain 1e-5;
+    the single-pass ones: within their derived allowance."""
     nlon, nlat, p, seed, nsteps = 360, 180, 4, 3, 500
     key = ("run500", nlon, nlat, p, seed)
     o, u = case(nlon, nlat, p, seed)
@@ -240,10 +250,87 @@ def test_precision_config_360x180_p4_500_steps(prec):
         errs.append((np.linalg.norm(d) / np.linalg.norm(want[..., f, :]), np.abs(d).max() / np.abs(want[..., f, :]).max()))
     print(f"\n{prec} 360x180 p=4, 500 steps: rel L2 / max per field (h, hu, hv):",
           " ".join("%.2e/%.2e" % e for e in errs), "mass drift %.1e" % (m1 / m0 - 1))
-    tol = 1e-5 if prec == "fp32" else C * OPS[prec][1]
-    for f in range(3):
-        d = np.abs(got[..., f, :] - want[..., f, :]).max()
-        bound = (0.0 if prec == "fp32" else nsteps * dt * tol * S[..., f, :].max()) + \
-            1e-5 * np.abs(want[..., f, :]).max()
-        assert d <= bound, (f, d, bound)
+    if prec == "fp32" or prec in SPLIT:
+        for f, (l2, mx) in enumerate(errs):
+            assert l2 <= 1e-5 and mx <= 1e-5, (prec, f, l2, mx)
+    else:
+        tol = C * OPS[prec][1]
+        for f in range(3):
+            d = np.abs(got[..., f, :] - want[..., f, :]).max()
+            bound = nsteps * dt * tol * S[..., f, :].max() + 1e-5 * np.abs(want[..., f, :]).max()
+            assert d <= bound, (f, d, bound)
     assert abs(m1 / m0 - 1) < 1e-9
+
+
+# ------------------------------------------------------------ split operands --
+
+def state_errs(got, want):
+    out = []
+    for f in range(3):
+        d = got[..., f, :] - want[..., f, :]
+        out.append((np.linalg.norm(d) / np.linalg.norm(want[..., f, :]), np.abs(d).max() / np.abs(want[..., f, :]).max()))
+    return out
+
+
+@pytest.mark.parametrize("prec", list(SPLIT))
+@pytest.mark.parametrize("nlon,nlat", MESHES)
+@pytest.mark.parametrize("p", [0, 1, 2, 3, 4])
+def test_split_rhs_matches_oracle(p, nlon, nlat, prec):
+    o, u = case(nlon, nlat, p, 21)
+    with dgswe.Solver(nlon, nlat, p, R, G, OMEGA, precision=prec) as s:
+        k = s.rhs(u)
+    tol = C * SPLIT[prec] + 1e-6
+    for f, (l2, mx) in enumerate(tend_err(k, o.rhs(u), o.rhs_magnitude(u))):
+        assert l2 <= tol and mx <= tol, (f, l2, mx, tol)
+
+
+@pytest.mark.parametrize("prec", list(SPLIT))
+@pytest.mark.parametrize("nlon,nlat,p,seed", [(180, 90, 3, 2), (360, 180, 4, 3)])
+def test_split_rhs_matches_oracle_full_size(nlon, nlat, p, seed, prec):
+    o, u = case(nlon, nlat, p, seed)
+    with dgswe.Solver(nlon, nlat, p, R, G, OMEGA, precision=prec) as s:
+        k = s.rhs(u)
+    errs = tend_err(k, o.rhs(u), o.rhs_magnitude(u))
+    print(prec, nlon, nlat, p, ["%.2e/%.2e" % e for e in errs])
+    tol = C * SPLIT[prec] + 1e-6
+    for f, (l2, mx) in enumerate(errs):
+        assert l2 <= tol and mx <= tol, (f, l2, mx, tol)
+
+
+@pytest.mark.parametrize("prec", list(SPLIT))
+@pytest.mark.parametrize("nlon,nlat,p,seed,nsteps", [(20, 10, 1, 1, 100), (64, 32, 4, 4, 60), (180, 90, 3, 2, 1000)])
+def test_split_steps_match_oracle_within_fp32_tolerance(nlon, nlat, p, seed, nsteps, prec):
+    """States after 100 (20x10, degree 1), 60 (64x32, degree 4) and 1000
+    (180x90, degree 3) SSP-RK3 steps: plain per-field 1e-5, mass to 1e-9."""
+    key = ("run", nlon, nlat, p, seed, nsteps)
+    o, u = case(nlon, nlat, p, seed)
+    if key not in _cache:
+        o.set_threads(os.cpu_count() or 1)
+        dt = o.max_dt(u, 0.1)
+        _cache[key] = (dt, o.step(u, nsteps, dt, 3))
+    dt, want = _cache[key]
+    with dgswe.Solver(nlon, nlat, p, R, G, OMEGA, precision=prec) as s:
+        s.set_option(dgswe.OPT_STEPS_PER_GRAPH, 50)
+        s.set_state(u)
+        m0 = s.total_mass()
+        s.step(nsteps, dt)
+        got = s.get_state()
+        m1 = s.total_mass()
+    errs = state_errs(got, want)
+    print(f"\n{prec} {nlon}x{nlat} p={p}, {nsteps} steps: rel L2 / max (h, hu, hv):",
+          " ".join("%.2e/%.2e" % e for e in errs))
+    for f, (l2, mx) in enumerate(errs):
+        assert l2 <= 1e-5 and mx <= 1e-5, (prec, f, l2, mx)
+    assert abs(m1 / m0 - 1) < 1e-9, (m0, m1)
+
+
+def test_split_is_closer_to_fp32_than_single_pass():
+    nlon, nlat, p = 60, 30, 3
+    o, u = case(nlon, nlat, p, 12)
+    ks = {}
+    for pr in ("fp32", "fp32_tc_fp16", "fp32_tc_bf16x3", "fp32_tc_fp16x3"):
+        with dgswe.Solver(nlon, nlat, p, R, G, OMEGA, precision=pr) as s:
+            ks[pr] = s.rhs(u)
+    S = o.rhs_magnitude(u)
+    e = {pr: max(m for _, m in tend_err(ks[pr], ks["fp32"], S)) for pr in ks if pr != "fp32"}
+    assert e["fp32_tc_fp16x3"] < e["fp32_tc_bf16x3"] < e["fp32_tc_fp16"], e
