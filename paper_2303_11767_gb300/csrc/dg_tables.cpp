@@ -157,8 +157,11 @@ int dg_build_tables(HostTables &t, int nlon, int nlat, int p, double R, double g
             r.cosn[q] = std::cos(th);
             r.sinn[q] = std::sin(th);
         }
-        r.ce_s = (j == 0) ? 0.0 : std::cos(tb);
-        r.ce_n = (j == nlat - 1) ? 0.0 : std::cos(tb + t.dth);
+        // the edge between rows j and j + 1 gets one value, whichever row
+        // reads it: the two tiles (or bands) that meet there evaluate that
+        // edge's flux from the same bits
+        r.ce_s = (j == 0) ? 0.0 : std::cos(-0.5 * M_PI + j * t.dth);
+        r.ce_n = (j == nlat - 1) ? 0.0 : std::cos(-0.5 * M_PI + (j + 1) * t.dth);
         for (int b = 0; b < n; ++b)
             for (int c = 0; c < n; ++c) r.Ci[b][c] = Ci[b * n + c];
         for (int b = 0; b < n; ++b)

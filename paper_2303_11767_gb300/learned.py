@@ -114,10 +114,14 @@ def row_statistics(T, nlon, nlat):
     return rows, om.astype(np.float32), sd.astype(np.float32)
 
 
-def train(X, T, epochs=8, batch=4096, lr=1e-3, seed=0, log=print, row_norm=False):
+def train(X, T, epochs=8, batch=4096, lr=1e-3, seed=0, log=print, row_norm=False, input_noise=0.0):
     """row_norm: targets normalised per latitude row (the coarse mesh's error
     depends on latitude, which the 60 inputs do not carry); the library then
-    denormalises the network output with the row statistics."""
+    denormalises the network output with the row statistics.
+    input_noise: every batch's inputs get fresh Gaussian noise of this many
+    standard deviations per feature (targets unchanged), so the network also
+    sees states off the projected-fine ones the corrected coarse run drifts
+    into, and its output varies slowly across them."""
     import torch
 
     mlp = dgswe.MLP(60, 128, 12, seed=seed)
@@ -133,6 +137,7 @@ def train(X, T, epochs=8, batch=4096, lr=1e-3, seed=0, log=print, row_norm=False
     mlp.set_normalization(in_mean, in_std, out_mean, out_std)
     dX = torch.from_numpy(X).cuda()
     dT = torch.from_numpy(T).cuda()
+    dstd = torch.from_numpy(in_std.astype(np.float32)).cuda()
     n = X.shape[0]
     g = torch.Generator(device="cuda")
     g.manual_seed(seed)
@@ -144,6 +149,8 @@ def train(X, T, epochs=8, batch=4096, lr=1e-3, seed=0, log=print, row_norm=False
         for b0 in range(0, n - batch + 1, batch):
             idx = perm[b0:b0 + batch]
             xb = dX.index_select(0, idx).contiguous()
+            if input_noise > 0:
+                xb = (xb + input_noise * dstd * torch.randn(xb.shape, device="cuda", generator=g)).contiguous()
             tb = dT.index_select(0, idx).contiguous()
             lr_k = lr * 0.5 * (1 + math.cos(math.pi * steps / max(1, epochs * (n // batch))))
             losses.append(mlp.train_step(xb, tb, lr_k))
@@ -187,6 +194,44 @@ def evaluate(mlp, seed, horizon_s, checkpoints=4, spinup_s=1800.0, log=print):
                "mass_drift_learned": (learned.total_mass() - plain.total_mass()) / plain.total_mass()}
         log(json.dumps(row))
         out.append(row)
+    p.close()
+    return out
+
+
+def evaluate_many(mlps, seed, horizon_s, checkpoints=4, spinup_s=1800.0, log=print):
+    """evaluate() for several networks at once ({name: network}), against
+    one fine reference run: plain coarse DG and one learned coarse solver per
+    network, all from the projected fine state at the end of the spin-up."""
+    p = Pair(seed, spinup_s)
+    u0 = p.projected()
+    solvers = {"plain": dgswe.Solver(*COARSE, precision="fp32")}
+    for name in mlps:
+        solvers[name] = dgswe.Solver(*COARSE, precision="fp32")
+    for name, s in solvers.items():
+        s.set_state(u0)
+        s.set_option(dgswe.OPT_STEPS_PER_GRAPH, 64)
+        if name != "plain":
+            s.attach_mlp(mlps[name])
+    nsteps = int(round(horizon_s / p.tau))
+    out = []
+    done = 0
+    for c in range(1, checkpoints + 1):
+        k = nsteps * c // checkpoints - done
+        p.advance_fine(k)
+        for s in solvers.values():
+            s.step(k, p.tau)
+        done += k
+        ref = p.projected()
+        m_plain = solvers["plain"].total_mass()
+        row = {"hours": done * p.tau / 3600.0}
+        for name, s in solvers.items():
+            row[name] = rel_l2(s.get_state(), ref)
+            if name != "plain":
+                row["mass_drift_" + name] = (s.total_mass() - m_plain) / m_plain
+        log(json.dumps(row))
+        out.append(row)
+    for s in solvers.values():
+        s.close()
     p.close()
     return out
 

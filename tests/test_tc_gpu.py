@@ -18,7 +18,11 @@ a pair hi + lo of the 16-bit type, which represents it to u^2, and each
 product is A_hi B_hi + A_lo B_hi + A_hi B_lo; the neglected A_lo B_lo is of
 order u^2 too.  Their tendencies are held to C u^2 S plus the FP32
 tendency tolerance (1e-6 S), and their states to the plain per-field FP32
-tolerance 1e-5 (relative L2 and max), with no derived allowance.
+tolerance 1e-5 (relative L2 and max), with no derived allowance.  FP16 pairs
+also have an absolute floor: a residual below FP16's smallest normal (6.1e-5)
+is subnormal, spaced 2^-24, so an operand x is held to about 3e-8 / |x|; the
+smallest fluxes of a coarse degree-0 mesh (~0.03) put that near 1e-6, and the
+FP16-pair tendency bound gets 4e-6 S on top.
 """
 import os
 
@@ -35,6 +39,7 @@ torch = pytest.importorskip("torch")
 R, G, OMEGA = synth.EARTH_RADIUS, 9.80616, 7.292e-5
 OPS = {"fp32_tc_bf16": (0, 2.0 ** -9, torch.bfloat16), "fp32_tc_fp16": (1, 2.0 ** -12, torch.float16)}
 SPLIT = {"fp32_tc_bf16x3": 2.0 ** -18, "fp32_tc_fp16x3": 2.0 ** -24}   # u^2 of the pair
+SPLIT_FLOOR = {"fp32_tc_bf16x3": 1e-6, "fp32_tc_fp16x3": 4e-6}        # + FP32 rounding / FP16 subnormals
 C = 8.0
 _cache = {}
 
@@ -279,7 +284,7 @@ def test_split_rhs_matches_oracle(p, nlon, nlat, prec):
     o, u = case(nlon, nlat, p, 21)
     with dgswe.Solver(nlon, nlat, p, R, G, OMEGA, precision=prec) as s:
         k = s.rhs(u)
-    tol = C * SPLIT[prec] + 1e-6
+    tol = C * SPLIT[prec] + SPLIT_FLOOR[prec]
     for f, (l2, mx) in enumerate(tend_err(k, o.rhs(u), o.rhs_magnitude(u))):
         assert l2 <= tol and mx <= tol, (f, l2, mx, tol)
 
@@ -292,7 +297,7 @@ def test_split_rhs_matches_oracle_full_size(nlon, nlat, p, seed, prec):
         k = s.rhs(u)
     errs = tend_err(k, o.rhs(u), o.rhs_magnitude(u))
     print(prec, nlon, nlat, p, ["%.2e/%.2e" % e for e in errs])
-    tol = C * SPLIT[prec] + 1e-6
+    tol = C * SPLIT[prec] + SPLIT_FLOOR[prec]
     for f, (l2, mx) in enumerate(errs):
         assert l2 <= tol and mx <= tol, (f, l2, mx, tol)
 
