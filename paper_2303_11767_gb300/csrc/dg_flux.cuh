@@ -56,6 +56,11 @@ __device__ __forceinline__ void check_depth(T h, unsigned &st)
     if (!(h > T(0))) st |= (h != h) ? DG_STATUS_NONFINITE : DG_STATUS_NONPHYSICAL;
 }
 
+// Every multiply-add below is an explicit fma: these functions are inlined at
+// several call sites (an edge's flux is evaluated by whichever tile or band
+// owns it), and left to the compiler's contraction the same edge could round
+// differently at two sites.
+
 // Physical lambda-flux (hu, hu u + P, hu v) of a state q = (h', hu, hv) with
 // h = href + h' and the pressure P = g h' (href + h'/2) (the constant part
 // g href^2/2 is carried by the rho table), and the wave speed |u| + sqrt(g h).
@@ -65,9 +70,9 @@ __device__ __forceinline__ void lam_flux(const T *q, T href, T g, T *f, T &speed
     const T h = href + q[0];
     check_depth(h, st);
     const T u = q[1] * rcp(h);
-    const T P = q[0] * g * (href + T(0.5) * q[0]);
+    const T P = (q[0] * g) * fma(T(0.5), q[0], href);
     f[0] = q[1];
-    f[1] = q[1] * u + P;
+    f[1] = fma(q[1], u, P);
     f[2] = q[2] * u;
     speed = fabs(u) + wave_sqrt(g * h);
 }
@@ -78,10 +83,10 @@ __device__ __forceinline__ void th_flux(const T *q, T href, T g, T *f, T &speed,
     const T h = href + q[0];
     check_depth(h, st);
     const T v = q[2] * rcp(h);
-    const T P = q[0] * g * (href + T(0.5) * q[0]);
+    const T P = (q[0] * g) * fma(T(0.5), q[0], href);
     f[0] = q[2];
     f[1] = q[1] * v;
-    f[2] = q[2] * v + P;
+    f[2] = fma(q[2], v, P);
     speed = fabs(v) + wave_sqrt(g * h);
 }
 
@@ -96,9 +101,9 @@ __device__ __forceinline__ void rusanov_lam(const T *L, const T *R, T href, T g,
     T fl[3], fr[3], al, ar;
     lam_flux(L, href, g, fl, al, st);
     lam_flux(R, href, g, fr, ar, st);
-    const T a = aglob > T(0) ? aglob : fmax(al, ar);   // global mode: the stage's largest |u| + c
+    const T ha = T(0.5) * (aglob > T(0) ? aglob : fmax(al, ar));   // global mode: the stage's largest |u| + c
 #pragma unroll
-    for (int f = 0; f < 3; ++f) out[f] = cF * (T(0.5) * (fl[f] + fr[f]) - T(0.5) * a * (R[f] - L[f]));
+    for (int f = 0; f < 3; ++f) out[f] = cF * fma(-ha, R[f] - L[f], T(0.5) * (fl[f] + fr[f]));
 }
 
 // Rusanov flux through a theta-face, lower state S, upper state N, times the
@@ -110,9 +115,9 @@ __device__ __forceinline__ void rusanov_th(const T *S, const T *Nq, T href, T g,
     T fs[3], fn[3], as, an;
     th_flux(S, href, g, fs, as, st);
     th_flux(Nq, href, g, fn, an, st);
-    const T a = aglob > T(0) ? aglob : fmax(as, an);   // global mode: the stage's largest |v| + c
+    const T ha = T(0.5) * (aglob > T(0) ? aglob : fmax(as, an));   // global mode: the stage's largest |v| + c
 #pragma unroll
-    for (int f = 0; f < 3; ++f) out[f] = cGce * (T(0.5) * (fs[f] + fn[f]) - T(0.5) * a * (Nq[f] - S[f]));
+    for (int f = 0; f < 3; ++f) out[f] = cGce * fma(-ha, Nq[f] - S[f], T(0.5) * (fs[f] + fn[f]));
 }
 
 }  // namespace dgk

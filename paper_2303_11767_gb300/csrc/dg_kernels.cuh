@@ -408,17 +408,19 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &A, int bx, int by
     // ---- S4 halo: traces of the ring of neighbour elements facing the tile
     cp_async_wait_all();   // the ring's modes are in shared memory
     __syncthreads();
-    {
-        // one item per (ring element, field): its N traces on the side that
-        // faces the tile, each mode row read once.  The sums run in the order
-        // the owning tile uses for the element's own traces (lambda edge:
-        // sum_b L_b(eta_k) (sum_a L_a(+-1) u[b][a]); theta edge:
+    if constexpr (N >= 5) {
+        // degree 4: one item per (ring element, field), its N traces on the
+        // side that faces the tile, each mode row read once (a third of the
+        // instructions of one item per trace point; measured +9 % at 1440x720
+        // and 360x180, while up to degree 3 the shorter per-point items keep
+        // more threads busy on the one-wave 180x90 mesh).  The sums run in
+        // the order the owning tile uses for the element's own traces (lambda
+        // edge: sum_b L_b(eta_k) (sum_a L_a(+-1) u[b][a]); theta edge:
         // sum_b L_b(+-1) (sum_a L_a(xi_k) u[b][a])), so both tiles of a tile
         // boundary evaluate that edge's flux from the same bits and the
         // single-valued flux keeps mass to roundoff.
         const int nH = 2 * Wv + nSe + nNe;
-        // whole warps take halo items (no divergence inside a warp); more
-        // items than threads only for degree 0 in 4-row tiles
+        // whole warps take halo items (no divergence inside a warp)
         for (int it = tid; it < 3 * nH; it += 32 * W) {
             const int r = it / 3, f = it - 3 * r;
             int side, sl, hh;
@@ -469,6 +471,70 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &A, int bx, int by
             T *slot = trc + sl * TRC + (side * 3 + f) * N;
 #pragma unroll
             for (int kk = 0; kk < N; ++kk) slot[kk] = acc[kk];
+        }
+    } else {
+        // up to degree 3: one item per trace point (ring element, side, k),
+        // the same sums in the same order
+        const int nWE = Wv * N;
+        const int nS = hasS ? Gv * N : 0, nN = hasN ? Gv * N : 0;
+        const int it = tid;   // whole warps take halo items (no divergence inside a warp)
+        if (it < 2 * nWE + nS + nN) {
+            int side, kk, sl, hh;
+            if (it < 2 * nWE) {                 // west / east halo columns
+                const bool east = it >= nWE;
+                const int r = east ? it - nWE : it;
+                const int w = r / N;
+                kk = r - w * N;
+                side = east ? 0 : 1;            // east halo needs its W trace
+                sl = (w + 1) * TW + (east ? Gv + 1 : 0);
+                hh = east ? Wv + w : w;
+            } else {                            // south / north halo rows
+                const int r0 = it - 2 * nWE;
+                const bool north = r0 >= nS;
+                const int r = north ? r0 - nS : r0;
+                const int c = r / N;
+                kk = r - c * N;
+                side = north ? 2 : 3;           // north halo needs its S trace
+                sl = (north ? Wv + 1 : 0) * TW + c + 1;
+                hh = 2 * Wv + (north ? nSe + c : c);
+            }
+            // row b of field f of the halo element's stage state
+            auto halo_row = [&](int f, int b, T *row) {
+                const T *hb = ef + hh * EL + f * NP + b * N;
+#pragma unroll
+                for (int a = 0; a < N; ++a) row[a] = hb[a];
+                if (has_inc) {
+#pragma unroll
+                    for (int a = 0; a < N; ++a) row[a] += hb[GE::HALO_CAP + a];
+                }
+            };
+            T *slot = trc + sl * TRC;
+#pragma unroll
+            for (int f = 0; f < 3; ++f) {
+                T acc = T(0);
+                if (side <= 1) {                // lambda edge: sum_b L_b(eta_kk) sum_a L_a(+-1) u[b][a]
+#pragma unroll
+                    for (int b = 0; b < N; ++b) {
+                        T row[N];
+                        halo_row(f, b, row);
+                        T s = T(0);
+#pragma unroll
+                        for (int a = 0; a < N; ++a) s = fma(side == 1 ? B.SE[a] : B.SW[a], row[a], s);
+                        acc = fma(B.LV[b][kk], s, acc);
+                    }
+                } else {                        // theta edge: sum_b L_b(+-1) sum_a L_a(xi_kk) u[b][a]
+#pragma unroll
+                    for (int b = 0; b < N; ++b) {
+                        T row[N];
+                        halo_row(f, b, row);
+                        T s = T(0);
+#pragma unroll
+                        for (int a = 0; a < N; ++a) s = fma(B.LV[a][kk], row[a], s);
+                        acc = fma(side == 3 ? B.SE[b] : B.SW[b], s, acc);
+                    }
+                }
+                slot[(side * 3 + f) * N + kk] = acc;
+            }
         }
     }
     __syncthreads();
