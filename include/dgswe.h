@@ -262,6 +262,14 @@ dg_status dg_band_unpack(dg_handle h, int side, const void *d_in);
  * dt and, with DG_OPT_CHECK_FINITE, the status is read as in dg_step. */
 dg_status dg_band_stage(dg_handle h, double dt);
 
+/* The two terms of the CFL step of dg_max_dt over the band's own rows:
+ * *H = min over the rows and Gauss points of min(R dth, R cos(theta) dlam)
+ * and *c = max over the Gauss points of sqrt(u^2 + v^2) + sqrt(g h).  The
+ * whole mesh's step is cfl * min(H) / (max(p, 1) * max(c)) over the bands
+ * (the smallest H and the largest c may sit in different bands, so the
+ * bands' own steps do not give it).  Works on any sphere handle. */
+dg_status dg_band_cfl_terms(dg_handle h, double *H, double *c);
+
 /* The band's mass as the compensated (Neumaier) pair of its fixed-order
  * reduction: the band's mass is R^2 (sum + err); merging the bands' pairs in
  * band order with an error-free two-sum gives the whole mesh's mass. */

@@ -165,13 +165,27 @@ def advance(bands, exchange, nsteps: int, dt: float, rk_order: int = 3):
 
 
 def global_min(dist, value: float, torch) -> float:
-    """Minimum over ranks (the CFL step of the whole mesh is the smallest of
-    the bands' steps)."""
+    """Minimum over ranks."""
     if dist is None:
         return float(value)
     t = torch.tensor([value], dtype=torch.float64)
     dist.all_reduce(t, op=dist.ReduceOp.MIN)
     return float(t.item())
+
+
+def global_dt(dist, terms, cfl: float, degree: int, torch) -> float:
+    """The whole mesh's CFL step cfl * H / (max(p, 1) c) from every rank's
+    terms (H, c) (dg_band_cfl_terms): H = the smallest, c = the largest over
+    the bands, so the step equals the one the whole-mesh solver computes.
+    terms: this rank's (H, c), or a list of the (H, c) of the bands in this
+    process when dist is None."""
+    if dist is None:
+        pairs = terms if isinstance(terms, list) else [terms]
+        H, c = min(h for h, _ in pairs), max(v for _, v in pairs)
+    else:
+        H = global_min(dist, terms[0], torch)
+        c = -global_min(dist, -terms[1], torch)
+    return cfl * H / (max(degree, 1) * c)
 
 
 def global_mass(dist, pair, radius: float, torch) -> float:

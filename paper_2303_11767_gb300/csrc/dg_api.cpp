@@ -1105,13 +1105,14 @@ dg_status dg_total_mass_device(dg_handle h, double *d_mass)
     return enqueue_mass(h, d_mass);
 }
 
-dg_status dg_max_dt(dg_handle h, double cfl, double *dt)
+}  // extern "C"
+
+namespace {
+// The two terms of the CFL step of the resident state: H = min over the
+// rows and Gauss points of min(R dth, R cos(theta) dlam), c = max over the
+// Gauss points of sqrt(u^2 + v^2) + sqrt(g h).
+dg_status cfl_terms(dg_ctx *h, double *H_out, double *c_out)
 {
-    if (dg_status s = check(h)) return s;
-    if (h->physics != 0) return planar_unsupported(h, "dg_max_dt");
-    if (!dt || !(cfl > 0)) return fail(DG_EINVAL, "need cfl > 0 and dt != NULL");
-    if (!h->have_state) return fail(DG_EINVAL, "no state set");
-    DeviceGuard dg(h->device);
     CUDA_TRY(cudaMemsetAsync(h->d_maxbits, 0, sizeof(unsigned long long), h->stream));
     int r = h->prec == DG_PREC_FP64
                 ? dg_launch_max_speed<double>(static_cast<const double *>(h->B[h->cur]), h->nlon, h->nlat, h->n,
@@ -1129,8 +1130,35 @@ dg_status dg_max_dt(dg_handle h, double cfl, double *dt)
     for (int j = 0; j < h->nlat; ++j)
         for (int q = 0; q < h->n; ++q)
             H = std::min(H, std::min(h->R * h->tab.dth, h->R * h->tab.rows[j].cosn[q] * h->tab.dlam));
+    *H_out = H;
+    *c_out = c;
+    return DG_OK;
+}
+}  // namespace
+
+extern "C" {
+
+dg_status dg_max_dt(dg_handle h, double cfl, double *dt)
+{
+    if (dg_status s = check(h)) return s;
+    if (h->physics != 0) return planar_unsupported(h, "dg_max_dt");
+    if (!dt || !(cfl > 0)) return fail(DG_EINVAL, "need cfl > 0 and dt != NULL");
+    if (!h->have_state) return fail(DG_EINVAL, "no state set");
+    DeviceGuard dg(h->device);
+    double H, c;
+    if (dg_status s = cfl_terms(h, &H, &c)) return s;
     *dt = cfl * H / (std::max(h->p, 1) * c);
     return DG_OK;
+}
+
+dg_status dg_band_cfl_terms(dg_handle h, double *H, double *c)
+{
+    if (dg_status s = check(h)) return s;
+    if (h->physics != 0) return planar_unsupported(h, "dg_band_cfl_terms");
+    if (!H || !c) return fail(DG_EINVAL, "H and c must not be NULL");
+    if (!h->have_state) return fail(DG_EINVAL, "no state set");
+    DeviceGuard dg(h->device);
+    return cfl_terms(h, H, c);
 }
 
 dg_status dg_projection_nodes(dg_handle h, double *lam, size_t nlam, double *theta, size_t ntheta)

@@ -100,6 +100,7 @@ SIGNATURES = {
     "dg_band_unpack": (ctypes.c_int, [_H, ctypes.c_int, ctypes.c_void_p]),
     "dg_band_stage": (ctypes.c_int, [_H, ctypes.c_double]),
     "dg_band_mass_pair": (ctypes.c_int, [_H, _dp, _dp]),
+    "dg_band_cfl_terms": (ctypes.c_int, [_H, _dp, _dp]),
 }
 
 _lib = None
@@ -230,6 +231,12 @@ class Solver:
     def stage(self, dt):
         """The next RK stage of the current step (dg_band_stage)."""
         _check(lib().dg_band_stage(self._h, float(dt)), self._h)
+
+    def cfl_terms(self):
+        """(H, c) of the CFL step over this handle's rows (dg_band_cfl_terms)."""
+        a, b = ctypes.c_double(), ctypes.c_double()
+        _check(lib().dg_band_cfl_terms(self._h, ctypes.byref(a), ctypes.byref(b)), self._h)
+        return a.value, b.value
 
     def mass_pair(self):
         """(sum, err): the band's mass is radius^2 (sum + err)."""

@@ -168,8 +168,9 @@ def _rank_main(rank, world, port, out_dir):
         pair = (float(np.sum(u0[jb:je, :, 0])), 1e-9 * (rank + 1))
         mass = bands.global_mass(dist, pair, 1.0, torch)
         dmin = bands.global_min(dist, 100.0 + rank, torch)
+        dglob = bands.global_dt(dist, (10.0 - rank, 3.0 + rank), 0.5, 2, torch)
         np.save(os.path.join(out_dir, f"band{rank}.npy"), b.state())
-        np.save(os.path.join(out_dir, f"scalars{rank}.npy"), np.array([jb, je, href, mass, dmin]))
+        np.save(os.path.join(out_dir, f"scalars{rank}.npy"), np.array([jb, je, href, mass, dmin, dglob]))
     finally:
         dist.destroy_process_group()
 
@@ -189,9 +190,11 @@ def test_band_split_matches_single_rank_bitwise(world, tmp_path):
     href_single = 0.5 * float(np.cumsum(u0[..., 0].ravel())[-1]) / (NLAT * NLON)
     pairs = []
     for r in range(world):
-        jb, je, href, mass, dmin = np.load(tmp_path / f"scalars{r}.npy")
+        jb, je, href, mass, dmin, dglob = np.load(tmp_path / f"scalars{r}.npy")
         assert href == href_single
         assert dmin == 100.0
+        # smallest H and largest c of all ranks: 0.5 (10 - (world - 1)) / (2 (3 + world - 1))
+        assert dglob == 0.5 * (10.0 - (world - 1)) / (2 * (3.0 + world - 1))
         pairs.append((float(np.sum(u0[int(jb):int(je), :, 0])), 1e-9 * (r + 1)))
     # mass: the pairs merged in rank order with the error-free two-sum
     want_mass = math.fsum([a for a, _ in pairs]) + sum(b for _, b in pairs)
