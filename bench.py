@@ -42,6 +42,8 @@ WORKLOADS = {
     "c1": (20, 10, 1, 100, 1, "20x10 elements, degree 1, SSP-RK3, 100 steps per bench step, seed 1"),
     "c3": (360, 180, 4, 500, 3, "360x180 elements, degree 4, SSP-RK3, 500 steps per bench step, seed 3"),
     "r1": (1440, 720, 4, 20, 3, "1440x720 elements, degree 4, SSP-RK3, 20 steps per bench step, seed 3"),
+    # profiling size that still streams (78 MB per FP32 array, 3-5 arrays per stage)
+    "r2": (720, 360, 4, 20, 3, "720x360 elements, degree 4, SSP-RK3, 20 steps per bench step, seed 3"),
 }
 ENSEMBLE_DESC = ("256 members, nlat uniform on 20..180, nlon = 2 nlat, degree uniform on 1..4, "
                  "member k seed 1000+k, FP32 SSP-RK3, 10 steps per bench step, one persistent launch per stage")
