@@ -198,6 +198,31 @@ def evaluate(mlp, seed, horizon_s, checkpoints=4, spinup_s=1800.0, log=print):
     return out
 
 
+def scaled_copy(mlp, norm, alpha):
+    """A copy of a trained network whose learned source is alpha times the
+    original (the output statistics scaled; same weights): shrinking a
+    correction that overshoots."""
+    c = dgswe.MLP(60, 128, 12, seed=0)
+    c.set_params(mlp.get_params())
+    c.set_normalization(norm["in_mean"], norm["in_std"], alpha * norm["out_mean"], alpha * norm["out_std"])
+    if "row_mean" in norm:
+        c.set_row_normalization(alpha * norm["row_mean"], alpha * norm["row_std"])
+    return c
+
+
+def parse_variant(spec):
+    """'name[:key=value,...]' with keys noise (input noise), row_norm (0/1),
+    alpha (shrinkage of the learned source), epochs."""
+    name, _, rest = spec.partition(":")
+    kw = {"noise": 0.0, "row_norm": 0, "alpha": 1.0, "epochs": None}
+    for item in filter(None, rest.split(",")):
+        k, v = item.split("=")
+        if k not in kw:
+            raise ValueError(f"unknown variant key {k}")
+        kw[k] = float(v)
+    return name, kw
+
+
 def evaluate_many(mlps, seed, horizon_s, checkpoints=4, spinup_s=1800.0, log=print):
     """evaluate() for several networks at once ({name: network}), against
     one fine reference run: plain coarse DG and one learned coarse solver per
@@ -248,7 +273,12 @@ def main():
     ap.add_argument("--out", default="learned_result.json")
     ap.add_argument("--params-out", default="")
     ap.add_argument("--row-norm", action="store_true", help="normalise the targets per latitude row")
+    ap.add_argument("--variant", action="append", default=[],
+                    help="name[:noise=s,row_norm=0|1,alpha=a,epochs=e]; several variants are trained on the "
+                         "same pairs and evaluated against one fine reference run")
     args = ap.parse_args()
+    if args.variant:
+        return main_variants(args)
     t0 = time.time()
     X, T = generate(args.pairs, args.train_seeds, stride=args.stride, target_steps=args.target_steps)
     t_gen = time.time() - t0
@@ -263,6 +293,34 @@ def main():
         json.dump(res, fh, indent=1)
     if args.params_out:
         np.savez(args.params_out, params=mlp.get_params(), **norm)
+    print(json.dumps(res["evaluation"][-1]))
+
+
+def main_variants(args):
+    """Train every --variant on one set of pairs and evaluate them all
+    against one fine reference run (evaluate_many)."""
+    t0 = time.time()
+    X, T = generate(args.pairs, args.train_seeds, stride=args.stride, target_steps=args.target_steps)
+    t_gen = time.time() - t0
+    trained, mlps, hist = {}, {}, {}
+    for spec in args.variant:
+        name, kw = parse_variant(spec)
+        key = (kw["noise"], kw["row_norm"], kw["epochs"])
+        if key not in trained:     # variants that differ only in alpha share one network
+            trained[key] = train(X, T, epochs=int(kw["epochs"] or args.epochs), row_norm=bool(kw["row_norm"]),
+                                 input_noise=kw["noise"], log=lambda s: None)
+        mlp, norm, h = trained[key]
+        mlps[name] = mlp if kw["alpha"] == 1.0 else scaled_copy(mlp, norm, kw["alpha"])
+        hist[name] = h
+        print(name, kw, "loss", ["%.4f" % v for v in h], flush=True)
+    t_train = time.time() - t0 - t_gen
+    ev = evaluate_many(mlps, args.test_seed, args.horizon_hours * 3600.0)
+    res = {"pairs": args.pairs, "samples": int(X.shape[0]), "train_seeds": args.train_seeds,
+           "target_steps": args.target_steps, "stride": args.stride, "test_seed": args.test_seed,
+           "variants": args.variant, "loss_history": hist, "evaluation": ev,
+           "seconds": {"generate": t_gen, "train": t_train, "evaluate": time.time() - t0 - t_gen - t_train}}
+    with open(args.out, "w") as fh:
+        json.dump(res, fh, indent=1)
     print(json.dumps(res["evaluation"][-1]))
 
 
