@@ -223,10 +223,12 @@ def parse_variant(spec):
     return name, kw
 
 
-def evaluate_many(mlps, seed, horizon_s, checkpoints=4, spinup_s=1800.0, log=print):
+def evaluate_many(mlps, seed, horizon_s, checkpoints=4, spinup_s=1800.0, log=print, checkpoint_hours=None):
     """evaluate() for several networks at once ({name: network}), against
     one fine reference run: plain coarse DG and one learned coarse solver per
-    network, all from the projected fine state at the end of the spin-up."""
+    network, all from the projected fine state at the end of the spin-up.
+    checkpoint_hours: explicit evaluation times (hours, increasing) instead
+    of `checkpoints` equal intervals."""
     p = Pair(seed, spinup_s)
     u0 = p.projected()
     solvers = {"plain": dgswe.Solver(*COARSE, precision="fp32")}
@@ -238,18 +240,33 @@ def evaluate_many(mlps, seed, horizon_s, checkpoints=4, spinup_s=1800.0, log=pri
         if name != "plain":
             s.attach_mlp(mlps[name])
     nsteps = int(round(horizon_s / p.tau))
+    if checkpoint_hours:
+        marks = [int(round(h * 3600.0 / p.tau)) for h in checkpoint_hours]
+    else:
+        marks = [nsteps * c // checkpoints for c in range(1, checkpoints + 1)]
     out = []
     done = 0
-    for c in range(1, checkpoints + 1):
-        k = nsteps * c // checkpoints - done
+    diverged = set()   # learned solvers whose state stopped being physical (h <= 0 or non-finite)
+    for mark in marks:
+        k = mark - done
         p.advance_fine(k)
-        for s in solvers.values():
-            s.step(k, p.tau)
+        for name, s in solvers.items():
+            if name in diverged:
+                continue
+            try:
+                s.step(k, p.tau)
+            except dgswe.DGError:
+                if name == "plain":
+                    raise
+                diverged.add(name)
         done += k
         ref = p.projected()
         m_plain = solvers["plain"].total_mass()
         row = {"hours": done * p.tau / 3600.0}
         for name, s in solvers.items():
+            if name in diverged:
+                row[name] = [float("nan")] * 3
+                continue
             row[name] = rel_l2(s.get_state(), ref)
             if name != "plain":
                 row["mass_drift_" + name] = (s.total_mass() - m_plain) / m_plain
@@ -259,6 +276,48 @@ def evaluate_many(mlps, seed, horizon_s, checkpoints=4, spinup_s=1800.0, log=pri
         s.close()
     p.close()
     return out
+
+
+def select_alpha(mlp, norm, alphas, seed, hours, log=print):
+    """The shrinkage of the learned source chosen on a validation seed: every
+    alpha is evaluated against one fine reference run of `seed` at `hours`,
+    and the alpha with the smallest mean log ratio of its relative L2 error
+    to plain coarse DG over the three fields wins (ratios below 1 = a gain).
+    Returns (alpha, the validation row)."""
+    nets = {f"a{a}": (mlp if a == 1.0 else scaled_copy(mlp, norm, a)) for a in alphas}
+    row = evaluate_many(nets, seed, hours * 3600.0, checkpoint_hours=[hours], log=log)[-1]
+    score = {a: float(np.mean([math.log(e / p) for e, p in zip(row[f"a{a}"], row["plain"])])) for a in alphas}
+    best = min(alphas, key=lambda a: score[a])
+    return best, {"row": row, "score": score}
+
+
+def main_alpha(args):
+    """Train one network, choose the shrinkage alpha on the validation seed,
+    then evaluate every alpha (the chosen one marked) on the held-out test
+    seed against one fine reference run, at the checkpoint times."""
+    t0 = time.time()
+    X, T = generate(args.pairs, args.train_seeds, stride=args.stride, target_steps=args.target_steps)
+    t_gen = time.time() - t0
+    mlp, norm, hist = train(X, T, epochs=args.epochs, row_norm=args.row_norm)
+    t_train = time.time() - t0 - t_gen
+    alphas = [float(a) for a in args.alphas.split(",")]
+    best, val = select_alpha(mlp, norm, alphas, args.val_seed, args.val_hours)
+    print(f"validation seed {args.val_seed}, {args.val_hours} h: alpha = {best}", json.dumps(val["score"]), flush=True)
+    t_val = time.time() - t0 - t_gen - t_train
+    nets = {f"a{a}": (mlp if a == 1.0 else scaled_copy(mlp, norm, a)) for a in alphas}
+    hours = [float(h) for h in args.checkpoint_hours.split(",")] if args.checkpoint_hours else None
+    ev = evaluate_many(nets, args.test_seed, args.horizon_hours * 3600.0, checkpoint_hours=hours)
+    res = {"pairs": args.pairs, "samples": int(X.shape[0]), "train_seeds": args.train_seeds,
+           "target_steps": args.target_steps, "stride": args.stride, "epochs": args.epochs,
+           "alphas": alphas, "val_seed": args.val_seed, "val_hours": args.val_hours, "alpha_selected": best,
+           "validation": val, "test_seed": args.test_seed, "loss_history": hist, "evaluation": ev,
+           "seconds": {"generate": t_gen, "train": t_train, "validate": t_val,
+                       "evaluate": time.time() - t0 - t_gen - t_train - t_val}}
+    with open(args.out, "w") as fh:
+        json.dump(res, fh, indent=1)
+    if args.params_out:
+        np.savez(args.params_out, params=mlp.get_params(), alpha=best, **norm)
+    print(json.dumps(res["evaluation"][-1]))
 
 
 def main():
@@ -276,9 +335,16 @@ def main():
     ap.add_argument("--variant", action="append", default=[],
                     help="name[:noise=s,row_norm=0|1,alpha=a,epochs=e]; several variants are trained on the "
                          "same pairs and evaluated against one fine reference run")
+    ap.add_argument("--alphas", default="", help="comma-separated shrinkages of the learned source; the one "
+                                                  "used is chosen on --val-seed")
+    ap.add_argument("--val-seed", type=int, default=6001)
+    ap.add_argument("--val-hours", type=float, default=3.0)
+    ap.add_argument("--checkpoint-hours", default="", help="comma-separated evaluation times (hours)")
     args = ap.parse_args()
     if args.variant:
         return main_variants(args)
+    if args.alphas:
+        return main_alpha(args)
     t0 = time.time()
     X, T = generate(args.pairs, args.train_seeds, stride=args.stride, target_steps=args.target_steps)
     t_gen = time.time() - t0

@@ -173,8 +173,8 @@ def test_pipeline_end_to_end_reports_plain_vs_learned(capsys):
     """Reduced pipeline (64 pairs of one training run, 2 epochs, 1 h on a
     held-out seed): it runs on the library kernels end to end, the learned
     solver keeps mass, and the comparison with plain coarse DG is reported.
-    The full-size comparison (2000 pairs, 12 h) is recorded with its numbers
-    in profiles/learned_correction_c5.md."""
+    The full-size comparison is recorded with its numbers in
+    profiles/learned_correction_c5.md."""
     X, T = learned.generate(64, [5000], spinup_s=600.0, stride=8, target_steps=8, log=lambda s: None)
     assert X.shape == (64 * 2592, 60) and T.shape == (64 * 2592, 12)
     assert np.isfinite(X).all() and np.isfinite(T).all()
@@ -184,11 +184,25 @@ def test_pipeline_end_to_end_reports_plain_vs_learned(capsys):
     assert all(np.isfinite(ev["plain"])) and all(np.isfinite(ev["learned"]))
     assert abs(ev["mass_drift_learned"]) < 1e-9
     with capsys.disabled():
-        print("\nlearned correction, 1 h, relative L2 (h, hu, hv): plain", ["%.2e" % v for v in ev["plain"]],
-              "learned", ["%.2e" % v for v in ev["learned"]])
-    # what the network should gain: no field less accurate than plain coarse
-    # DG.  The reduced training here does not reach that; the loss is recorded
-    # as an expected failure (plain DG stays the default and the fallback)
-    # rather than hidden.
-    if not all(l <= p for l, p in zip(ev["learned"], ev["plain"])):
-        pytest.xfail("learned coarse solver less accurate than plain coarse DG after the reduced training")
+        print("\nlearned correction (reduced), 1 h, relative L2 (h, hu, hv): plain",
+              ["%.2e" % v for v in ev["plain"]], "learned", ["%.2e" % v for v in ev["learned"]])
+
+
+def test_learned_source_gains_over_plain_dg(capsys):
+    """What the trained network gains over the method without it: 300 pairs
+    of two training runs (targets over 8 coarse steps), 8 epochs; the
+    shrinkage of the learned source chosen on a validation seed (6001, 2 h)
+    among 0.5, 0.25, 0.1; then, on the held-out test seed 6000 after 3 h,
+    the learned coarse solver's relative L2 error against the projected fine
+    run is below plain coarse DG's in every field."""
+    X, T = learned.generate(300, [5000, 5001], stride=8, target_steps=8, log=lambda s: None)
+    mlp, norm, hist = learned.train(X, T, epochs=8, log=lambda s: None)
+    alpha, val = learned.select_alpha(mlp, norm, [0.5, 0.25, 0.1], 6001, 2.0, log=lambda s: None)
+    net = learned.scaled_copy(mlp, norm, alpha)
+    row = learned.evaluate_many({"learned": net}, 6000, 3 * 3600.0, checkpoint_hours=[3.0], log=lambda s: None)[-1]
+    with capsys.disabled():
+        print(f"\nlearned correction, alpha {alpha} (validation scores {val['score']}), 3 h on the test seed, "
+              "relative L2 (h, hu, hv): plain", ["%.2e" % v for v in row["plain"]],
+              "learned", ["%.2e" % v for v in row["learned"]])
+    assert abs(row["mass_drift_learned"]) < 1e-9
+    assert all(l < p for l, p in zip(row["learned"], row["plain"])), (row["learned"], row["plain"])
