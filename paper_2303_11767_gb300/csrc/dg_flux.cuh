@@ -49,6 +49,14 @@ __device__ __forceinline__ double wave_sqrt<double>(double x) { return sqrt(x); 
 template <>
 __device__ __forceinline__ float wave_sqrt<float>(float x) { return x * rsqrtf(x); }
 
+// Finiteness of many values with one test at the end: chk = fma(x, 0, chk)
+// for each x stays 0 while every x is finite and becomes NaN (for good) at
+// the first Inf or NaN (Inf * 0 = NaN); one FMA per value instead of a
+// compare and a predicated OR.  The rounding intrinsics keep the compiler
+// from dropping the product.
+__device__ __forceinline__ float nf_acc(float x, float chk) { return __fmaf_rn(x, 0.0f, chk); }
+__device__ __forceinline__ double nf_acc(double x, double chk) { return __fma_rn(x, 0.0, chk); }
+
 // h <= 0 makes u = hu/h meaningless; a NaN depth is reported as non-finite.
 template <typename T>
 __device__ __forceinline__ void check_depth(T h, unsigned &st)

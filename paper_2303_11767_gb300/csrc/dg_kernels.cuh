@@ -724,12 +724,12 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &A, int bx, int by
 
         if (valid) {
             const T cdt = A.cc * A.dt, adt = A.ca * A.dt;
+            T chk = T(0);   // non-finite tendency or state: NaN (nf_acc)
 #pragma unroll
             for (int f = 0; f < 3; ++f) {
                 const size_t off = e * EL + f * NP + k * N;
 #pragma unroll
-                for (int a = 0; a < N; ++a)
-                    if (!isfinite(kk[f][a])) st |= DG_STATUS_NONFINITE;
+                for (int a = 0; a < N; ++a) chk = nf_acc(kk[f][a], chk);
                 if (A.out_rhs) store_row<T, N>(A.out_rhs + off, kk[f]);
                 T inc[N];
                 if (has_inc) load_row<T, N>(incp + off, inc);
@@ -782,7 +782,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &A, int bx, int by
                             const float2 ol2 = __fadd2_rn(l1, neg2(__fadd2_rn(hi, neg2(s1))));
                             ob[a] = hi.x, ob[a + 1] = hi.y;
                             ol[a] = ol2.x, ol[a + 1] = ol2.y;
-                            if (!isfinite(hi.x) || !isfinite(hi.y)) st |= DG_STATUS_NONFINITE;
+                            chk = nf_acc(hi.y, nf_acc(hi.x, chk));
                         }
                     }
 #pragma unroll
@@ -795,12 +795,13 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &A, int bx, int by
                         const T hi = s1 + l1;
                         ob[a] = hi;
                         ol[a] = l1 - (hi - s1);
-                        if (!isfinite(hi)) st |= DG_STATUS_NONFINITE;
+                        chk = nf_acc(hi, chk);
                     }
                     store_row<T, N>(outb + off, ob);
                     if (A.out_lo) store_row<T, N>(A.out_lo + off, ol);
                 }
             }
+            if (!isfinite(chk)) st |= DG_STATUS_NONFINITE;
         }
     }
     if (st && valid) atomicOr(A.status, st);

@@ -755,6 +755,7 @@ __global__ void __launch_bounds__(128 * TC_TPE, TcSmem<N, SPLIT>::CTAS) tc_stage
         const size_t e0 = (size_t)j * rowlen + i;
         const float cdt = A.cc * A.dt, adt = A.ca * A.dt;
         const bool fin = A.out_base != nullptr;
+        float chk = 0.0f;   // non-finite tendency or state of an interior element: NaN (nf_acc)
 #pragma unroll 1
         for (int f = 0; f < 3; ++f) {
             const int b0 = ((part - f * N) % TC_TPE + TC_TPE) % TC_TPE;
@@ -799,7 +800,7 @@ __global__ void __launch_bounds__(128 * TC_TPE, TcSmem<N, SPLIT>::CTAS) tc_stage
                     for (int a = 0; a < N; ++a) {
                         const size_t o = ob + (size_t)(a * A.nlon);
                         const float kv = kk[a], inc = vinc[rr][a], acc = vacc[rr][a];
-                        if (!isfinite(kv)) st_int |= DG_STATUS_NONFINITE;
+                        chk = dgk::nf_acc(kv, chk);
                         if (A.out_rhs) A.out_rhs[o] = kv;
                         if (A.inc_out) A.inc_out[o] = fmaf(cdt, kv, A.ci * inc);
                         if (A.acc_out) A.acc_out[o] = fmaf(adt, kv, acc);
@@ -814,12 +815,13 @@ __global__ void __launch_bounds__(128 * TC_TPE, TcSmem<N, SPLIT>::CTAS) tc_stage
                             const float hi = s1 + l1;
                             A.out_base[o] = hi;
                             if (A.out_lo) A.out_lo[o] = l1 - (hi - s1);
-                            if (!isfinite(hi)) st_int |= DG_STATUS_NONFINITE;
+                            chk = dgk::nf_acc(hi, chk);
                         }
                     }
                 }
             }
         }
+        if (!isfinite(chk)) st_int |= DG_STATUS_NONFINITE;
     }
 
     dgk::pdl_launch_dependents();
