@@ -258,8 +258,9 @@ dg_status dg_band_unpack(dg_handle h, int side, const void *d_in);
 
 /* Run the next stage of the current time step (stage 1, 2, ... of the RK
  * scheme of DG_OPT_RK_ORDER) with step size dt, which must stay the same
- * within a step.  After a step's last stage the simulated time advances by
- * dt and, with DG_OPT_CHECK_FINITE, the status is read as in dg_step. */
+ * within a step (DG_EINVAL otherwise); change DG_OPT_RK_ORDER only between
+ * steps.  After a step's last stage the simulated time advances by dt and,
+ * with DG_OPT_CHECK_FINITE, the status is read as in dg_step. */
 dg_status dg_band_stage(dg_handle h, double dt);
 
 /* The two terms of the CFL step of dg_max_dt over the band's own rows:

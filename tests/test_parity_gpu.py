@@ -32,7 +32,9 @@ pytestmark = pytest.mark.gpu
 
 R, G, OMEGA = synth.EARTH_RADIUS, 9.80616, 7.292e-5
 TOL = {"fp64": 1e-12, "fp32": 1e-5}
-TEND_TOL = {"fp64": 3e-14, "fp32": 1e-6}
+TEND_TOL = {"fp64": 3e-14, "fp32": 1e-6,
+            # split FP16 operands: 8 u^2 of the pair plus the FP16-pair subnormal floor (tests/test_tc_gpu.py)
+            "fp32_tc_fp16x3": 8 * 2.0 ** -24 + 4e-6}
 NTHREADS = os.cpu_count() or 1
 
 
@@ -170,7 +172,8 @@ def test_rk_orders(order):
 
 # ---------------------------------------------------- global Rusanov alpha --
 
-@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32", 1e-5), ("fp32_tc_fp16", 8 * 2.0 ** -12)])
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32", 1e-5), ("fp32_tc_fp16", 8 * 2.0 ** -12),
+                                      ("fp32_tc_fp16x3", 1e-5)])
 def test_global_alpha_mode_matches_oracle(prec, tol):
     nlon, nlat, p = 44, 14, 3
     o = oracle_sphere(nlon, nlat, p)
@@ -368,7 +371,8 @@ def test_zero_steps_change_nothing(prec):
 
 # --------------------------------------------------------- well-balanced option --
 
-@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32", 1e-5), ("fp32_tc_fp16", 8 * 2.0 ** -12)])
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32", 1e-5), ("fp32_tc_fp16", 8 * 2.0 ** -12),
+                                      ("fp32_tc_fp16x3", 1e-5)])
 def test_well_balanced_option_matches_oracle(prec, tol):
     nlon, nlat, p = 44, 14, 3
     u = case(nlon, nlat, p, 15)[1]
