@@ -103,6 +103,66 @@ def generate(n_pairs, seeds, spinup_s=1800.0, stride=4, target_steps=1, log=prin
     return np.concatenate(X).astype(np.float32), np.concatenate(T).astype(np.float32)
 
 
+def prolong(u, r, nf):
+    """The modal state, on the mesh refined r x r with nf points per
+    direction, of the same piecewise polynomial as the coarse state u
+    [nlat, nlon, 3, nc^2] (nested meshes: a coarse polynomial restricted to a
+    sub-element is one of degree nc - 1 <= nf - 1 there, so this is exact):
+    per direction T[s][a_f][a_c] = int L_af(x) L_ac((x + 2s + 1)/r - 1) dx,
+    exact with max(nf, nc) + 1 Gauss points."""
+    from numpy.polynomial import legendre as npleg
+
+    nlat, nlon, nfld, ncp = u.shape
+    nc = int(round(math.sqrt(ncp)))
+    x, w = npleg.leggauss(max(nf, nc) + 1)
+
+    def L(k, t):
+        c = np.zeros(k + 1)
+        c[k] = 1.0
+        return math.sqrt((2 * k + 1) / 2.0) * npleg.legval(t, c)
+
+    T = np.array([[[np.sum(w * L(af, x) * L(ac, (x + 2 * sub + 1) / r - 1)) for ac in range(nc)] for af in range(nf)]
+                  for sub in range(r)])
+    uf = np.einsum("yBb,xAa,jifba->jyixfBA", T, T, u.reshape(nlat, nlon, nfld, nc, nc))
+    return np.ascontiguousarray(uf.reshape(nlat * r, nlon * r, nfld, nf * nf))
+
+
+def generate_local(n_pairs, seeds, spinup_s=1800.0, stride=8, target_steps=8, log=print):
+    """Pairs whose inputs are states of the plain coarse trajectory and whose
+    targets are the coarse scheme's own error over k coarse steps at that
+    state: the fine mesh starts from the same piecewise polynomial (exact
+    prolongation, `prolong`), both meshes advance k coarse steps and
+        target = [P(Phi_fine^k(L u_c)) - Phi_coarse^k(u_c)] / (k tau).
+    The network then sees at training the states it meets at run time (the
+    coarse run's, not projections of the fine run's)."""
+    X, T = [], []
+    per = int(math.ceil(n_pairs / len(seeds)))
+    t0 = time.time()
+    r = FINE[0] // COARSE[0]
+    for seed in seeds:
+        p = Pair(seed, spinup_s)
+        traj = dgswe.Solver(*COARSE, precision="fp32", check_finite=True)
+        probe = dgswe.Solver(*COARSE, precision="fp32", check_finite=True)
+        traj.set_state(p.projected())
+        for _ in range(per):
+            if len(X) >= n_pairs:
+                break
+            uc = traj.get_state()
+            p.fine.set_state(prolong(uc, r, FINE[2] + 1))
+            p.advance_fine(target_steps)
+            u1 = p.projected()
+            probe.set_state(uc)
+            probe.step(target_steps, p.tau)
+            X.append(gather_inputs(uc))
+            T.append(((u1 - probe.get_state()) / (target_steps * p.tau)).reshape(-1, 12))
+            traj.step(stride, p.tau)
+        log(f"seed {seed}: {len(X)} pairs (coarse trajectory), {time.time() - t0:.0f} s")
+        for x in (traj, probe):
+            x.close()
+        p.close()
+    return np.concatenate(X).astype(np.float32), np.concatenate(T).astype(np.float32)
+
+
 def row_statistics(T, nlon, nlat):
     """Per latitude row mean and std of the targets [n_samples, 12] (samples
     are whole coarse meshes in element order); stds floored at 1e-6 of the
@@ -296,7 +356,8 @@ def main_alpha(args):
     then evaluate every alpha (the chosen one marked) on the held-out test
     seed against one fine reference run, at the checkpoint times."""
     t0 = time.time()
-    X, T = generate(args.pairs, args.train_seeds, stride=args.stride, target_steps=args.target_steps)
+    gen = generate_local if args.local_targets else generate
+    X, T = gen(args.pairs, args.train_seeds, stride=args.stride, target_steps=args.target_steps)
     t_gen = time.time() - t0
     mlp, norm, hist = train(X, T, epochs=args.epochs, row_norm=args.row_norm)
     t_train = time.time() - t0 - t_gen
@@ -309,6 +370,7 @@ def main_alpha(args):
     ev = evaluate_many(nets, args.test_seed, args.horizon_hours * 3600.0, checkpoint_hours=hours)
     res = {"pairs": args.pairs, "samples": int(X.shape[0]), "train_seeds": args.train_seeds,
            "target_steps": args.target_steps, "stride": args.stride, "epochs": args.epochs,
+           "targets": "coarse-trajectory local error" if args.local_targets else "projected fine run",
            "alphas": alphas, "val_seed": args.val_seed, "val_hours": args.val_hours, "alpha_selected": best,
            "validation": val, "test_seed": args.test_seed, "loss_history": hist, "evaluation": ev,
            "seconds": {"generate": t_gen, "train": t_train, "validate": t_val,
@@ -340,6 +402,8 @@ def main():
     ap.add_argument("--val-seed", type=int, default=6001)
     ap.add_argument("--val-hours", type=float, default=3.0)
     ap.add_argument("--checkpoint-hours", default="", help="comma-separated evaluation times (hours)")
+    ap.add_argument("--local-targets", action="store_true",
+                    help="inputs from the plain coarse trajectory, targets its own k-step error (generate_local)")
     args = ap.parse_args()
     if args.variant:
         return main_variants(args)
