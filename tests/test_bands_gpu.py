@@ -19,14 +19,15 @@ TOL = {"fp64": 1e-12, "fp32": 1e-5}
 NTHREADS = os.cpu_count() or 1
 
 
-def _run_bands(u0, nlon, nlat, p, prec, nb, nsteps, dt, rk, torch):
+def _run_bands(u0, nlon, nlat, p, prec, nb, nsteps, dt, rk, torch, wb=0):
     stream = torch.cuda.Stream()
     rows = [bands.band_rows(nlat, nb, k) for k in range(nb)]
     bs = [dgswe.Solver.band(nlon, nlat, jb, je, p, R, G, OMEGA, precision=prec, rk_order=rk) for jb, je in rows]
     ex = bands.LocalExchange(bs, torch, torch.float64 if prec == "fp64" else torch.float32, stream)
     href = bands.reference_depth(None, u0[:, :, 0, 0], 0, 1, torch)
     for b, (jb, je) in zip(bs, rows):
-        if prec != "fp64":
+        b.set_option(dgswe.OPT_WELL_BALANCED, wb)
+        if prec != "fp64" or wb:
             b.set_reference_depth(href)
         b.set_state(u0[jb:je])
     bands.advance(bs, ex, nsteps, dt, rk)
@@ -39,8 +40,9 @@ def _run_bands(u0, nlon, nlat, p, prec, nb, nsteps, dt, rk, torch):
     return out, mass, dt_glob
 
 
-def _whole(u0, nlon, nlat, p, prec, nsteps, dt, rk, torch):
+def _whole(u0, nlon, nlat, p, prec, nsteps, dt, rk, torch, wb=0):
     with dgswe.Solver(nlon, nlat, p, R, G, OMEGA, precision=prec, rk_order=rk) as s:
+        s.set_option(dgswe.OPT_WELL_BALANCED, wb)
         s.set_state(u0)
         s.step(nsteps, dt)
         return s.get_state(), s.total_mass(), s.max_dt(0.1)   # the step of the final state, as for the bands
@@ -78,6 +80,21 @@ def test_bands_every_rk_order(rk):
         got, _, _ = _run_bands(u0, nlon, nlat, p, prec, 3, 5, dt, rk, torch)
         want, _, _ = _whole(u0, nlon, nlat, p, prec, 5, dt, rk, torch)
         assert np.array_equal(got, want), (prec, rk)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_bands_well_balanced_equal_whole_mesh(prec):
+    """The well-balanced option on bands: every band removes the rest-state
+    tendency of the same reference depth (the whole mesh's, given to each band),
+    so the bands still equal the whole mesh bit for bit."""
+    torch = pytest.importorskip("torch")
+    nlon, nlat, p = 24, 12, 2
+    o = O.Oracle.sphere(nlon, nlat, p, R, G, OMEGA)
+    u0 = o.project_tensor(synth.SmoothField(23).fields_grid)
+    dt = o.max_dt(u0, 0.1)
+    got, _, _ = _run_bands(u0, nlon, nlat, p, prec, 3, 6, dt, 3, torch, wb=1)
+    want, _, _ = _whole(u0, nlon, nlat, p, prec, 6, dt, 3, torch, wb=1)
+    assert np.array_equal(got, want), np.abs(got - want).max()
 
 
 def test_band_refuses_what_needs_the_whole_mesh():
