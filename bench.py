@@ -79,6 +79,9 @@ def parse():
     ap.add_argument("--precision", default="fp32", choices=sorted(DTYPES))
     ap.add_argument("--rk-steps", type=int, default=0, help="override RK steps per bench step")
     ap.add_argument("--no-extras", action="store_true", help="skip fp64-plain, e2e and cpu legs (profiling)")
+    ap.add_argument("--bands", type=int, default=0,
+                    help="time the workload split into this many latitude bands on one GPU (band exchange "
+                         "through device copies) against the whole-mesh solver")
     return ap.parse_args()
 
 
@@ -483,6 +486,76 @@ def streaming_leg(prec, torch, stream, flush, make_prec, reps=3, nsteps=20):
             "kernel": KERNELS[prec].format(n=p + 1)}
 
 
+def run_bands(args, world, rank, local):
+    """The latitude-band decomposition on one GPU: the workload's mesh as
+    args.bands bands, each an independent handle (dg_create_band), their
+    boundary rows exchanged before every stage by device copies on one stream
+    (bands.LocalExchange), every stage launched per band (dg_band_stage),
+    against the whole-mesh solver (graph replay) in the same run.  Measures
+    what the decomposition itself costs: the exchange and the per-band
+    launches."""
+    import torch
+
+    from paper_2303_11767_gb300 import bands, dgswe
+
+    nlon, nlat, p, nsteps, seed, desc = WORKLOADS[args.workload]
+    if args.rk_steps:
+        nsteps = args.rk_steps
+    dof = 3 * (p + 1) ** 2 * nlon * nlat
+    torch.cuda.set_device(local)
+    dgswe.set_device(local)
+    stream = torch.cuda.Stream()
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    whole = dgswe.Solver(nlon, nlat, p, precision=args.precision, check_finite=False)
+    whole.set_option(dgswe.OPT_STREAM, stream.cuda_stream)
+    whole.set_option(dgswe.OPT_STEPS_PER_GRAPH, min(nsteps, 1024))
+    u0 = initial_state(whole, seed)
+    whole.set_state(u0)
+    dt = whole.max_dt(CFL)
+    rows = [bands.band_rows(nlat, args.bands, k) for k in range(args.bands)]
+    bs = [dgswe.Solver.band(nlon, nlat, jb, je, p, precision=args.precision, check_finite=False) for jb, je in rows]
+    ex = bands.LocalExchange(bs, torch, torch.float64 if args.precision == "fp64" else torch.float32, stream)
+    href = bands.reference_depth(None, u0[:, :, 0, 0], 0, 1, torch)
+    for b, (jb, je) in zip(bs, rows):
+        if args.precision != "fp64":
+            b.set_reference_depth(href)
+        b.set_state(u0[jb:je])
+
+    def timed(fn):
+        ms = []
+        with torch.cuda.stream(stream):
+            for it in range(args.warmup + args.steps):
+                flush.zero_()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                fn()
+                b.record(stream)
+                b.synchronize()
+                if it >= args.warmup:
+                    ms.append(a.elapsed_time(b))
+        return ms
+
+    t_whole = timed(lambda: whole.step(nsteps, dt))
+    t_bands = timed(lambda: bands.advance(bs, ex, nsteps, dt, 3))
+    same = bool(np.array_equal(np.concatenate([b.get_state() for b in bs], axis=0), whole.get_state())) \
+        if args.warmup + args.steps > 0 else None
+    v_whole = dof * 3 * nsteps * len(t_whole) / (sum(t_whole) * 1e-3)
+    v_bands = dof * 3 * nsteps * len(t_bands) / (sum(t_bands) * 1e-3)
+    msg = 2 * bs[0].halo_len * (4 if args.precision != "fp64" else 8)
+    out = {
+        "metric": METRIC, "value": v_bands, "unit": "DOF-updates/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": sum(t_bands) / len(t_bands), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": DTYPES[args.precision], "data": "synthetic",
+        "config": {"workload": desc, "bands": args.bands, "rows": rows, "rk_steps_per_step": nsteps,
+                   "exchange": "device copies on one stream, before every stage",
+                   "bytes_per_boundary_per_stage": msg},
+        "whole_mesh": {"value": v_whole, "ms_per_step": sum(t_whole) / len(t_whole)},
+        "bands_over_whole": v_bands / v_whole,
+        "bands_equal_whole_bitwise": same,
+    }
+    print(json.dumps(out))
+
+
 def main():
     args = parse()
     world, rank, local = dist_setup()
@@ -491,6 +564,9 @@ def main():
         return
     if args.workload == "c4":
         run_ensemble(args, world, rank, local)
+        return
+    if args.bands:
+        run_bands(args, world, rank, local)
         return
     import torch
 
