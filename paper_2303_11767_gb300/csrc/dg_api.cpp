@@ -146,9 +146,10 @@ void free_state_buffers(dg_ctx *h)
 dg_status alloc_state_buffers(dg_ctx *h)
 {
     // a band's arrays carry its ghost rows around the own rows; the pointers
-    // kept point at own row 0
+    // kept point at own row 0.  The length is rounded up to 16 bytes: the
+    // stage kernel copies halo elements in whole 16-byte blocks.
     const size_t es = elem_size(h->prec);
-    const size_t bytes = (h->len + (size_t)(h->gs + h->gn) * h->row_len()) * es;
+    const size_t bytes = ((h->len + (size_t)(h->gs + h->gn) * h->row_len()) * es + 15) / 16 * 16;
     h->ghost_bytes = (size_t)h->gs * h->row_len() * es;
     std::vector<void **> want = {&h->B[0], &h->B[1], &h->I[0], &h->I[1], &h->D};
     if (h->f32()) {

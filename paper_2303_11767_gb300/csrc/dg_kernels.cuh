@@ -71,8 +71,11 @@ struct Geo {
     static constexpr int EW_OFF = 3 * N * SA;   // [f][2][N]
     static constexpr int X_OFF = 0;             // [f][2][alpha][SA]   (reuses T1/EW)
     static constexpr int WB_MIN = 6 * N * SA;
-    // element stride in the warp buffer, padded to spread groups over banks
-    static constexpr int WB = WB_MIN + ((N - (WB_MIN % 32)) % 32 + 32) % 32;
+    // element stride in the warp buffer, padded to spread groups over banks:
+    // congruent to N modulo 32, or at degree 4 to -N (the same bank pattern,
+    // 10 words shorter, which leaves room for the aligned halo ring)
+    static constexpr int WB = N == 5 ? WB_MIN + ((-N - (WB_MIN % 32)) % 32 + 64) % 32
+                                     : WB_MIN + ((N - (WB_MIN % 32)) % 32 + 32) % 32;
     static constexpr int TW = G + 2;            // padded tile width (halo columns)
     static constexpr int TH = W + 2;            // padded tile height (halo rows)
     // slot strides padded so that the N lanes of the G elements of a warp
@@ -80,8 +83,6 @@ struct Geo {
     static constexpr int TRC = bank_free_stride(12 * N, N, 32 / N);   // traces W,E,S,N x 3 x N
     static constexpr int EFC = bank_free_stride(6 * N, N, 32 / N);    // edge fluxes W,S x 3 x N
     static constexpr int HALO_MAX = 2 * W * N + 2 * G * N;
-    // values of one copy of the halo ring's modes (at most 2 W + 2 G elements)
-    static constexpr int HALO_CAP = (2 * W + 2 * G) * EL;
     static_assert(HALO_MAX <= 32 * W, "halo items exceed the block");
     static_assert(W * N + G * N <= 32 * W, "boundary flux items exceed the block");
 };
@@ -91,33 +92,41 @@ struct Geo {
 // the Rusanov phase, so the halo ring's modes (stage base, then increment)
 // are staged there first; it starts on a 16-byte boundary for the
 // asynchronous copies and is as long as the larger of the two uses.
+//
+// The ring is always copied in 16-byte pieces.  Where an element's modes are
+// a multiple of 16 bytes (degrees 1 and 3), the elements are 16-byte aligned
+// in global memory and sit back to back in the ring.  Otherwise (degrees 0, 2
+// and 4) each ring element gets a slot of RS values starting on a 16-byte
+// boundary and lands at offset s = (its global address / sizeof(T)) mod VA in
+// it, so that source and destination agree modulo 16 bytes: the copy covers
+// the aligned 16-byte blocks that hold the element, a few values of the
+// neighbouring elements included (the state arrays start on a 16-byte
+// boundary and are padded to a multiple of 16 bytes, so every block read
+// lies inside the array).
 template <typename T, int N, int W>
 struct SmemMap {
     using GE = Geo<N, W>;
     static constexpr int VA = 16 / (int)sizeof(T);
+    static constexpr bool PACKED = (GE::EL * (int)sizeof(T)) % 16 == 0;
+    static constexpr int RS = PACKED ? GE::EL : (GE::EL + 2 * (VA - 1)) / VA * VA;   // ring slot
+    static constexpr int PPS = RS / VA;                // 16-byte pieces per ring slot
+    // values of one copy of the halo ring (at most 2 W + 2 G elements)
+    static constexpr int HALO_CAP = (2 * W + 2 * GE::G) * RS;
     static constexpr int TRC_OFF = W * GE::G * GE::WB;
     static constexpr int EF_OFF = (TRC_OFF + GE::TW * GE::TH * GE::TRC + VA - 1) / VA * VA;
-    static constexpr int EF_LEN = GE::TW * GE::TH * GE::EFC > 2 * GE::HALO_CAP ? GE::TW * GE::TH * GE::EFC
-                                                                             : 2 * GE::HALO_CAP;
+    static constexpr int EF_LEN = GE::TW * GE::TH * GE::EFC > 2 * HALO_CAP ? GE::TW * GE::TH * GE::EFC : 2 * HALO_CAP;
     static constexpr size_t BYTES = sizeof(T) * (size_t)(EF_OFF + EF_LEN);
-    // bytes per asynchronous copy: the largest of 16 / 8 / 4 that divides an
-    // element's modes (elements are contiguous and the arrays 16-byte aligned)
-    static constexpr int CP = (GE::EL * (int)sizeof(T)) % 16 == 0 ? 16
-                              : (GE::EL * (int)sizeof(T)) % 8 == 0 ? 8
-                                                                   : 4;
+    static_assert(RS % VA == 0 && RS >= GE::EL + (PACKED ? 0 : VA - 1), "ring slot too short");
 };
 
-// Asynchronous global -> shared copy of CP bytes (both addresses CP-aligned);
-// it completes at cp_async_wait_all, and a block barrier then publishes it.
-template <int CP>
-__device__ __forceinline__ void cp_async(void *dst, const void *src)
+// Asynchronous global -> shared copy of 16 bytes (both addresses 16-byte
+// aligned); it completes at cp_async_wait_all, and a block barrier then
+// publishes it.
+__device__ __forceinline__ void cp_async16(void *dst, const void *src)
 {
     const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
     const size_t g = __cvta_generic_to_global(src);
-    if constexpr (CP == 16)
-        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(g) : "memory");
-    else
-        asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(d), "l"(g), "n"(CP) : "memory");
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(g) : "memory");
 }
 
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
@@ -308,34 +317,77 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &A, int bx, int by
     //      and the increment to ef[HALO_CAP, 2 HALO_CAP)
     const bool hasS = j0 > 0 || A.halo_s, hasN = j0 + Wv < A.nlat || A.halo_n;
     const int nSe = hasS ? Gv : 0, nNe = hasN ? Gv : 0;
-    {
-        constexpr int VPC = SM::CP / (int)sizeof(T), CPE = EL / VPC;
-        const int nH = 2 * Wv + nSe + nNe;
-        // The periodic W / E columns are found in the loop for 16-byte pieces
-        // (one or two per thread) and once before it for the 4- and 8-byte
-        // pieces (several per thread): the faster form measured for each.
-        constexpr bool WRAP_ONCE = SM::CP < 16;
-        const int iW = i0 > 0 ? i0 - 1 : A.nlon - 1, iE = i0 + Gv < A.nlon ? i0 + Gv : 0;   // i0 + Gv <= nlon
+    const int nH = 2 * Wv + nSe + nNe;
+    const int iW = i0 > 0 ? i0 - 1 : A.nlon - 1, iE = i0 + Gv < A.nlon ? i0 + Gv : 0;   // i0 + Gv <= nlon
+    // value offset of ring element h: W column, E column, S row, N row (hj =
+    // -1 is a neighbour band's row held just before row 0)
+    auto ring_off = [&](int h) -> long long {
+        int hj, hi;
+        if (h < 2 * Wv) {
+            const bool east = h >= Wv;
+            hj = j0 + (east ? h - Wv : h);
+            hi = east ? iE : iW;
+        } else {
+            const int r = h - 2 * Wv;
+            const bool north = r >= nSe;
+            hj = north ? j0 + Wv : j0 - 1;
+            hi = i0 + (north ? r - nSe : r);
+        }
+        return ((long long)hj * A.nlon + hi) * EL;
+    };
+    // position of a value within its 16-byte block
+    auto lead = [](const T *p) -> int {
+        return (int)((reinterpret_cast<uintptr_t>(p) / sizeof(T)) & (SM::VA - 1));
+    };
+    if constexpr (SM::PACKED) {
+        // the W / E columns found in the loop (one or two pieces per thread:
+        // measured faster than finding them once at degree 3)
+        constexpr int CPE = EL / SM::VA;
         for (int v = tid; v < nH * CPE; v += 32 * W) {
-            const int h = v / CPE, c = (v - h * CPE) * VPC;
+            const int h = v / CPE, c = (v - h * CPE) * SM::VA;
             int hj, hi;
             if (h < 2 * Wv) {
                 const bool east = h >= Wv;
                 hj = j0 + (east ? h - Wv : h);
-                if constexpr (WRAP_ONCE) hi = east ? iE : iW;
-                else hi = east ? (i0 + Gv) % A.nlon : (i0 - 1 + A.nlon) % A.nlon;
+                hi = east ? (i0 + Gv) % A.nlon : (i0 - 1 + A.nlon) % A.nlon;
             } else {
                 const int r = h - 2 * Wv;
                 const bool north = r >= nSe;
                 hj = north ? j0 + Wv : j0 - 1;
                 hi = i0 + (north ? r - nSe : r);
             }
-            // hj = -1 is a neighbour band's row held just before row 0
             const long long o = ((long long)hj * A.nlon + hi) * EL + c;
-            cp_async<SM::CP>(ef + h * EL + c, A.base + o);
-            if (has_inc) cp_async<SM::CP>(ef + GE::HALO_CAP + h * EL + c, incp + o);
+            cp_async16(ef + h * EL + c, A.base + o);
+            if (has_inc) cp_async16(ef + SM::HALO_CAP + h * EL + c, incp + o);
+        }
+    } else {
+        // piece c of ring slot h: the c-th 16-byte block from the one that
+        // holds the element's first value, while it still holds some of them
+        for (int v = tid; v < nH * SM::PPS; v += 32 * W) {
+            const int h = v / SM::PPS, c = v - h * SM::PPS;
+            const long long o = ring_off(h);
+            const T *sb = A.base + o;
+            const int lb = lead(sb);
+            if (c * SM::VA < lb + EL) cp_async16(ef + h * SM::RS + c * SM::VA, sb - lb + c * SM::VA);
+            if (has_inc) {
+                const T *si = incp + o;
+                const int li = lead(si);
+                if (c * SM::VA < li + EL)
+                    cp_async16(ef + SM::HALO_CAP + h * SM::RS + c * SM::VA, si - li + c * SM::VA);
+            }
         }
     }
+    // where ring element h's modes start in shared memory (base, increment)
+    auto ring_at = [&](int h, const T *&rb, const T *&ri) {
+        if constexpr (SM::PACKED) {
+            rb = ef + h * EL;
+            ri = rb + SM::HALO_CAP;
+        } else {
+            const long long o = ring_off(h);
+            rb = ef + h * SM::RS + lead(A.base + o);
+            ri = ef + SM::HALO_CAP + h * SM::RS + (has_inc ? lead(incp + o) : 0);
+        }
+    };
 
     // rows the epilogue will read: start moving them towards L1 now
     if (valid) {
@@ -419,7 +471,6 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &A, int bx, int by
         // sum_b L_b(+-1) (sum_a L_a(xi_k) u[b][a])), so both tiles of a tile
         // boundary evaluate that edge's flux from the same bits and the
         // single-valued flux keeps mass to roundoff.
-        const int nH = 2 * Wv + nSe + nNe;
         // whole warps take halo items (no divergence inside a warp)
         for (int it = tid; it < 3 * nH; it += 32 * W) {
             const int r = it / 3, f = it - 3 * r;
@@ -438,7 +489,10 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &A, int bx, int by
                 sl = (north ? Wv + 1 : 0) * TW + c + 1;
                 hh = 2 * Wv + (north ? nSe + c : c);
             }
-            const T *hb = ef + hh * EL + f * NP;
+            const T *hb, *hbi;
+            ring_at(hh, hb, hbi);
+            hb += f * NP;
+            hbi += f * NP;
             T acc[N];
 #pragma unroll
             for (int kk = 0; kk < N; ++kk) acc[kk] = T(0);
@@ -449,7 +503,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &A, int bx, int by
                 for (int a = 0; a < N; ++a) row[a] = hb[b * N + a];
                 if (has_inc) {
 #pragma unroll
-                    for (int a = 0; a < N; ++a) row[a] += hb[GE::HALO_CAP + b * N + a];
+                    for (int a = 0; a < N; ++a) row[a] += hbi[b * N + a];
                 }
                 if (side <= 1) {
                     T sb = T(0);
@@ -498,14 +552,16 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &A, int bx, int by
                 sl = (north ? Wv + 1 : 0) * TW + c + 1;
                 hh = 2 * Wv + (north ? nSe + c : c);
             }
+            const T *rb, *ri;
+            ring_at(hh, rb, ri);
             // row b of field f of the halo element's stage state
             auto halo_row = [&](int f, int b, T *row) {
-                const T *hb = ef + hh * EL + f * NP + b * N;
+                const T *hb = rb + f * NP + b * N, *hbi = ri + f * NP + b * N;
 #pragma unroll
                 for (int a = 0; a < N; ++a) row[a] = hb[a];
                 if (has_inc) {
 #pragma unroll
-                    for (int a = 0; a < N; ++a) row[a] += hb[GE::HALO_CAP + a];
+                    for (int a = 0; a < N; ++a) row[a] += hbi[a];
                 }
             };
             T *slot = trc + sl * TRC;
