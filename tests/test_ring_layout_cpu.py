@@ -70,7 +70,7 @@ def check_mesh(T, N, W, nlon, nlat, gs, gn, member_off=0):
 def test_aligned_ring_copy_stays_inside_the_arrays(T, N):
     assert ring_slot(T, N) % (16 // T) == 0 and ring_slot(T, N) >= 3 * N * N + 16 // T - 1
     n = 0
-    for W in (4, 8):
+    for W in (4, 8, 12):
         for nlon, nlat in MESHES:
             for gs, gn in [(0, 0), (1, 0), (0, 1), (1, 1)]:
                 n += check_mesh(T, N, W, nlon, nlat, gs, gn)
