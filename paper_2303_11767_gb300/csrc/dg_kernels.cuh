@@ -108,7 +108,11 @@ struct SmemMap {
     using GE = Geo<N, W>;
     static constexpr int VA = 16 / (int)sizeof(T);
     static constexpr bool PACKED = (GE::EL * (int)sizeof(T)) % 16 == 0;
-    static constexpr int RS = PACKED ? GE::EL : (GE::EL + 2 * (VA - 1)) / VA * VA;   // ring slot
+    // ring slot: room for the element at any offset in its first block, and
+    // an odd number of 16-byte blocks, so that the slots the lanes of a warp
+    // read in the halo-trace phase start in different banks
+    static constexpr int RS0 = (GE::EL + 2 * (VA - 1)) / VA * VA;
+    static constexpr int RS = PACKED ? GE::EL : (RS0 / VA) % 2 ? RS0 : RS0 + VA;
     static constexpr int PPS = RS / VA;                // 16-byte pieces per ring slot
     // values of one copy of the halo ring (at most 2 W + 2 G elements)
     static constexpr int HALO_CAP = (2 * W + 2 * GE::G) * RS;

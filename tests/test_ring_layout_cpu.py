@@ -16,7 +16,8 @@ MESHES = [(1, 3), (2, 9), (4, 2), (15, 19), (20, 10), (35, 19), (44, 14), (67, 1
 
 def ring_slot(T, N):
     EL, VA = 3 * N * N, 16 // T
-    return (EL + 2 * (VA - 1)) // VA * VA
+    rs = (EL + 2 * (VA - 1)) // VA * VA
+    return rs if (rs // VA) % 2 else rs + VA      # an odd number of 16-byte blocks
 
 
 def check_mesh(T, N, W, nlon, nlat, gs, gn, member_off=0):
