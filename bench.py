@@ -52,9 +52,9 @@ METRIC = "DOF-updates/s per RK stage (FP32/TC/learned vs FP64 plain) at stated L
 # (dram__bytes_read.sum + dram__bytes_write.sum, mean over the three SSP-RK3
 # stages, cold cache); only for kernels unchanged since that capture.
 TRAFFIC = {
-    ("fp32", "r1"): (998.3e6, "311.5 / 622.6 / 934.7 MB read, 263.4 / 278.6 / 584.2 MB written "
+    ("fp32", "r1"): (998.1e6, "311.5 / 622.9 / 934.6 MB read, 263.1 / 278.5 / 583.9 MB written "
                               "(1.20x the algorithmic 829.4 MB: the increment form's extra word, partly absorbed by L2)"),
-    ("fp32", "c3"): (39.36e6, "19.6 / 39.0 / 58.5 MB read, 0 / 0 / 1.0 MB written (the arrays stay in L2)"),
+    ("fp32", "c3"): (39.41e6, "19.6 / 39.0 / 58.5 MB read, 0 / 0 / 1.1 MB written (the arrays stay in L2)"),
 }
 CFL = 0.1
 FLUSH_BYTES = 256 << 20
