@@ -17,6 +17,10 @@ each precision from the FP64 path on the same mesh and, over a bounded
 sample, from the FP64 oracle, and (ii) the FP64 discretisation error: the
 FP64 solution against the FP64 solution of the same field on the 2x refined
 mesh at degree 4, as functions; the verdict "matches" = (i) <= 0.1 (ii).
+Beside the headline the line carries the tensor-core precisions, the FP64
+path, the 180 x 90 degree-3 mesh, the learned correction's 72 x 36 degree-1
+coarse solver with and without its network attached (`workload_c5`), the
+paper's planar timing workload and the end-to-end figure.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 Under torchrun each rank runs an independent replica (weak scaling).
@@ -707,6 +711,43 @@ def main():
             dof2 = 3 * (p2 + 1) ** 2 * n2 * l2_
             out["workload_c2"] = {"workload": desc2, "value": dof2 * 3 * ns2 * len(t2) / (sum(t2) * 1e-3),
                                   "dtype": "f32", "ms_per_step": sum(t2) / len(t2)}
+
+        # ---- the learned correction's coarse solver (72x36 degree 1, FP32),
+        #      plain and with the per-element network attached: random-init
+        #      weights, input statistics of the synthetic state and a source
+        #      scaled far below the tendency (the state keeps its trajectory),
+        #      so the difference is what the network's inference costs
+        from paper_2303_11767_gb300 import learned
+
+        n5, l5, p5 = learned.COARSE
+        ns5, sd5 = 200, 5
+        legs5 = {}
+        for with_mlp in (False, True):
+            sc5 = make_mesh(n5, l5, p5, "fp32", ns5)
+            u5 = initial_state(sc5, sd5)
+            sc5.set_state(u5)
+            dt5 = sc5.max_dt(learned.CFL_COARSE)
+            net = None
+            if with_mlp:
+                net = dgswe.MLP(seed=sd5)
+                X = learned.gather_inputs(u5)
+                xs = X.std(axis=0)
+                xs[xs == 0] = 1.0
+                ys = 1e-12 * np.abs(u5).reshape(-1, 12).max(axis=0) + 1e-30
+                net.set_normalization(X.mean(axis=0), xs, np.zeros(12), ys)
+                sc5.attach_mlp(net)
+            t5 = time_device(sc5, torch, stream, ns5, dt5, max(2, args.steps // 5), 1, mass_t, flush)
+            sc5.close()
+            if net is not None:
+                net.close()
+            dof5 = 3 * (p5 + 1) ** 2 * n5 * l5
+            legs5["learned" if with_mlp else "plain"] = {
+                "value": dof5 * 3 * ns5 * len(t5) / (sum(t5) * 1e-3), "ms_per_step": sum(t5) / len(t5)}
+        out["workload_c5"] = {"workload": f"{n5}x{l5} elements, degree {p5}, SSP-RK3, {ns5} steps per bench "
+                                          f"step, seed {sd5}; learned = the same with the per-element network "
+                                          "60-128-128-12 attached (random-init weights)",
+                              "dtype": "f32", **legs5,
+                              "learned_over_plain_time": legs5["learned"]["ms_per_step"] / legs5["plain"]["ms_per_step"]}
 
         # ---- the paper's own timing workload (planar geostrophic adjustment,
         #      50x50 elements, 360 RK4 steps of 100 s), FP64 planar kernel, with

@@ -530,7 +530,6 @@ class MLP:
         a = [np.ascontiguousarray(x, dtype=np.float32) for x in (in_mean, in_std, out_mean, out_std)]
         _check(lib().dg_mlp_set_normalization(self._h, *[_fptr(x) for x in a]))
 
-
     def set_row_normalization(self, out_mean_rows, out_std_rows):
         """Per-latitude-row output statistics [nlat, n_out] for the learned
         source; None removes them."""
@@ -540,6 +539,7 @@ class MLP:
         m = np.ascontiguousarray(out_mean_rows, dtype=np.float32)
         sd = np.ascontiguousarray(out_std_rows, dtype=np.float32)
         _check(lib().dg_mlp_set_row_normalization(self._h, int(m.shape[0]), _fptr(m), _fptr(sd)))
+
     def forward(self, x, y):
         _check(lib().dg_mlp_forward(self._h, ctypes.c_void_p(x.data_ptr()), int(x.shape[0]),
                                     ctypes.c_void_p(y.data_ptr())))
