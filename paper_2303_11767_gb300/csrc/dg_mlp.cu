@@ -519,57 +519,97 @@ dg_status dg_mlp_train_step(dg_mlp m, const float *d_x, const float *d_t, int ba
 
 namespace {
 
-// One thread per coarse element of a degree-1 mesh: gather the element's and
-// its four neighbours' modes (zeros across a pole), normalise, run the
-// network with BF16 weights and FP32 accumulation, and write the
-// de-normalised modal tendency.  The state is u_stage = base + inc with h
-// stored relative to href (mode 0 of h carries 2 href).
-__global__ void mlp_source_kernel(const float *__restrict__ base, const float *__restrict__ inc, float href, int nlon,
-                                  int nlat, const __nv_bfloat16 *__restrict__ wb, const float *__restrict__ wf,
-                                  size_t ob1, size_t oW2, size_t ob2, size_t oW3, size_t ob3,
-                                  const float *__restrict__ norm, const float *__restrict__ rownorm,
-                                  float *__restrict__ src)
+// One CTA of 128 threads (one per hidden unit) evaluates the network for
+// SRC_EPC consecutive coarse elements of a degree-1 mesh: gather each
+// element's and its four neighbours' modes (zeros across a pole), normalise
+// them into shared memory, then every thread forms its hidden unit of the
+// first and of the second layer for all the CTA's elements (BF16 weights,
+// FP32 accumulation), and the outputs (element, q) are spread over the
+// threads.  Every sum starts at its bias and runs over inputs / units in
+// index order, exactly as an evaluation of one element at a time.  The
+// state is u_stage = base + inc with h stored relative to href (mode 0 of h
+// carries 2 href).
+constexpr int SRC_EPC = 8;
+
+__global__ void __launch_bounds__(128) mlp_source_kernel(
+    const float *__restrict__ base, const float *__restrict__ inc, float href, int nlon, int nlat,
+    const __nv_bfloat16 *__restrict__ wb, const float *__restrict__ wf, size_t ob1, size_t oW2, size_t ob2,
+    size_t oW3, size_t ob3, const float *__restrict__ norm, const float *__restrict__ rownorm,
+    float *__restrict__ src)
 {
-    constexpr int NIN = 60, H = 128, NOUT = 12, PER = 12;
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= nlon * nlat) return;
-    const int j = e / nlon, i = e - j * nlon;
-    const int nb[5] = {e, j * nlon + (i + nlon - 1) % nlon, j * nlon + (i + 1) % nlon, j > 0 ? e - nlon : -1,
-                       j < nlat - 1 ? e + nlon : -1};
-    float x[NIN];
-#pragma unroll
-    for (int s = 0; s < 5; ++s)
-#pragma unroll
-        for (int v = 0; v < PER; ++v) {
+    constexpr int NIN = 60, H = 128, NOUT = 12, PER = 12, EPC = SRC_EPC;
+    static_assert(EPC * NOUT <= H, "one output per thread");
+    __shared__ float xs[EPC][NIN];
+    __shared__ float hs[EPC][H];
+    const int nel = nlon * nlat;
+    const int e0 = blockIdx.x * EPC;
+    const int t = threadIdx.x;
+    for (int v = t; v < EPC * NIN; v += H) {
+        const int el = v / NIN, c = v - el * NIN;
+        const int e = e0 + el;
+        float xv = 0.0f;
+        if (e < nel) {
+            const int j = e / nlon, i = e - j * nlon;
+            const int s = c / PER, q = c - s * PER;
+            const int nb = s == 0   ? e
+                           : s == 1 ? j * nlon + (i + nlon - 1) % nlon
+                           : s == 2 ? j * nlon + (i + 1) % nlon
+                           : s == 3 ? (j > 0 ? e - nlon : -1)
+                                    : (j < nlat - 1 ? e + nlon : -1);
             float val = 0.0f;
-            if (nb[s] >= 0) {
-                const size_t o = (size_t)nb[s] * PER + v;
-                val = base[o] + (inc ? inc[o] : 0.0f) + (v == 0 ? 2.0f * href : 0.0f);
+            if (nb >= 0) {
+                const size_t o = (size_t)nb * PER + q;
+                val = base[o] + (inc ? inc[o] : 0.0f) + (q == 0 ? 2.0f * href : 0.0f);
             }
-            const int c = s * PER + v;
-            x[c] = (val - norm[c]) / norm[NIN + c];
+            xv = (val - norm[c]) / norm[NIN + c];
         }
-    float a1[H];
-    for (int o = 0; o < H; ++o) {
-        float z = wf[ob1 + o];
-        for (int c = 0; c < NIN; ++c) z = fmaf(__bfloat162float(wb[(size_t)o * NIN + c]), x[c], z);
-        a1[o] = gelu(z);
+        xs[el][c] = xv;
     }
-    float y[NOUT];
+    __syncthreads();
+    {   // first hidden layer, unit t
+        float z[EPC];
+        const float b = wf[ob1 + t];
 #pragma unroll
-    for (int o = 0; o < NOUT; ++o) y[o] = wf[ob3 + o];
-    for (int o = 0; o < H; ++o) {
-        float z = wf[ob2 + o];
-        for (int c = 0; c < H; ++c) z = fmaf(__bfloat162float(wb[oW2 + (size_t)o * H + c]), a1[c], z);
-        const float a2 = gelu(z);
+        for (int el = 0; el < EPC; ++el) z[el] = b;
+        for (int c = 0; c < NIN; ++c) {
+            const float w = __bfloat162float(wb[(size_t)t * NIN + c]);
 #pragma unroll
-        for (int q = 0; q < NOUT; ++q) y[q] = fmaf(__bfloat162float(wb[oW3 + (size_t)q * H + o]), a2, y[q]);
+            for (int el = 0; el < EPC; ++el) z[el] = fmaf(w, xs[el][c], z[el]);
+        }
+#pragma unroll
+        for (int el = 0; el < EPC; ++el) hs[el][t] = gelu(z[el]);
     }
-    // denormalise: per latitude row if row statistics are set, else globally
-    const float *om = rownorm ? rownorm + (size_t)j * NOUT : norm + 2 * NIN;
-    const float *os = rownorm ? rownorm + (size_t)(nlat + j) * NOUT : norm + 2 * NIN + NOUT;
+    __syncthreads();
+    float a2[EPC];
+    {   // second hidden layer, unit t
+        const float b = wf[ob2 + t];
 #pragma unroll
-    for (int q = 0; q < NOUT; ++q) src[(size_t)e * PER + q] = y[q] * os[q] + om[q];
+        for (int el = 0; el < EPC; ++el) a2[el] = b;
+        for (int c = 0; c < H; ++c) {
+            const float w = __bfloat162float(wb[oW2 + (size_t)t * H + c]);
+#pragma unroll
+            for (int el = 0; el < EPC; ++el) a2[el] = fmaf(w, hs[el][c], a2[el]);
+        }
+#pragma unroll
+        for (int el = 0; el < EPC; ++el) a2[el] = gelu(a2[el]);
+    }
+    __syncthreads();   // every thread has read the first layer's activations
+#pragma unroll
+    for (int el = 0; el < EPC; ++el) hs[el][t] = a2[el];
+    __syncthreads();
+    if (t < EPC * NOUT) {   // output q of element el
+        const int el = t / NOUT, q = t - el * NOUT;
+        const int e = e0 + el;
+        if (e < nel) {
+            float y = wf[ob3 + q];
+            for (int c = 0; c < H; ++c) y = fmaf(__bfloat162float(wb[oW3 + (size_t)q * H + c]), hs[el][c], y);
+            // denormalise: per latitude row if row statistics are set, else globally
+            const int j = e / nlon;
+            const float om = rownorm ? rownorm[(size_t)j * NOUT + q] : norm[2 * NIN + q];
+            const float os = rownorm ? rownorm[(size_t)(nlat + j) * NOUT + q] : norm[2 * NIN + NOUT + q];
+            src[(size_t)e * PER + q] = y * os + om;
+        }
+    }
 }
 
 // Keep the total mass: remove from mode (a=0, b=0) of h the mass the learned
@@ -607,7 +647,7 @@ int dg_mlp_launch_source(const dg_mlp_ctx *m, const float *base, const float *in
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const int nel = nlon * nlat;
     if (m->rownorm && m->rownorm_nlat != nlat) return 2;   // row statistics of another mesh
-    mlp_source_kernel<<<(nel + 63) / 64, 64, 0, s>>>(base, inc, href, nlon, nlat, m->wb, m->w, m->ob1, m->oW2, m->ob2,
+    mlp_source_kernel<<<(nel + SRC_EPC - 1) / SRC_EPC, 128, 0, s>>>(base, inc, href, nlon, nlat, m->wb, m->w, m->ob1, m->oW2, m->ob2,
                                                      m->oW3, m->ob3, m->norm, m->rownorm, src);
     mlp_massfix_kernel<<<1, 256, 0, s>>>(src, c0, nlon, nlat);
     return cudaPeekAtLastError() == cudaSuccess ? 0 : 1;
